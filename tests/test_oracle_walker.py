@@ -1,0 +1,196 @@
+"""Pins for the oracle's serial walker (Algorithm 1) and its budgets.
+
+* Philox4x32-10 against the published known-answer vectors.
+* Neighbour sampling is uniform on N(v) (Algorithm 1 samples X_i uniformly).
+* Enumerating every walk of length L <= 4 on small graphs gives
+  E[phi_hat | z] = phi(z) = z^T h^(L) (Eq. phi-rw-identity); the walker's
+  replicas reproduce it within CLT bounds.
+* L = 0 makes every replica equal, so Q_R = phi(z)^2 (Eq. Q-Ustat).
+* |U_p| <= 2(L+1)/d_min for every replica (Lemma 3.6).
+* With G = 1 the estimator is the plain mean of Q_R, unbiased for beta^(L)
+  (Lemmas 3.3 and 3.4).
+* THEORY budgets equal the hand-evaluated Eqs. B-value ... K-value.
+* PILOT budget reaches the relative-error target of Problem 1 on the tiny graph.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+from pw_inputs import barabasi_albert, complete_graph, er_cycle, query_seeds, uniform_pairs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def test_philox_known_answers(oracle_lib):
+    for row in _read_rows("philox_kat.txt"):
+        v = [int(x, 16) for x in row]
+        out = oracle.philox(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_neighbour_sampling_uniform(oracle_lib):
+    g = barabasi_albert(300, 3, 2)
+    v = int(np.argmax(g.degrees))  # a hub: largest neighbour list
+    nbrs = g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]]
+    d = len(nbrs)
+    m = 30 * d
+    first = np.array([oracle.walk(g, v, 1, 99, w)[1] for w in range(m)])
+    counts = np.array([(first == u).sum() for u in nbrs])
+    assert counts.sum() == m
+    chi2 = ((counts - m / d) ** 2 / (m / d)).sum()
+    # chi-square with d-1 dof: mean d-1, sd sqrt(2(d-1))
+    assert chi2 < (d - 1) + 6 * math.sqrt(2 * (d - 1))
+
+
+def test_trajectories_follow_edges(oracle_lib, tiny_graph):
+    g = tiny_graph
+    adj = set(zip(np.repeat(np.arange(g.n), g.degrees).tolist(), g.col_idx.tolist()))
+    for w in range(50):
+        tr = oracle.walk(g, 5, 40, 1234, w)
+        assert tr[0] == 5
+        assert all((int(a), int(b)) in adj for a, b in zip(tr[:-1], tr[1:]))
+
+
+def _walk_expectation(g, start, L, z):
+    """E_start[sum_{i<=L} z_{X_i}/d_{X_i}] by enumerating all walks."""
+    deg = g.degrees
+    dist = {start: 1.0}
+    total = 0.0
+    for i in range(L + 1):
+        total += sum(p * z[v] / deg[v] for v, p in dist.items())
+        if i == L:
+            break
+        nxt = {}
+        for v, p in dist.items():
+            for u in g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]]:
+                nxt[int(u)] = nxt.get(int(u), 0.0) + p / deg[v]
+        dist = nxt
+    return total
+
+
+@pytest.mark.parametrize("L", [0, 1, 2, 4])
+def test_walk_identity_enumeration(oracle_lib, L):
+    g = er_cycle(9, 0.35, 11)
+    s, t = 0, 5
+    h = exact.series_h(g.row_ptr, g.col_idx, g.n, s, t, L)
+    for k in range(4):
+        z = oracle.probe_vector(g.n, 2024, k)[0].astype(np.float64)
+        phi = float(z @ h)
+        enum = _walk_expectation(g, s, L, z) - _walk_expectation(g, t, L, z)
+        assert enum == pytest.approx(phi, rel=1e-12, abs=1e-14)
+
+
+def test_replicas_unbiased_for_phi(oracle_lib):
+    g = er_cycle(9, 0.35, 11)
+    s, t, L, seed = 0, 5, 4, 2024
+    R = 20000
+    cfg = oracle.budget_cfg(mode=oracle.MODE_FIXED, B=1, G=1, R=R)
+    out = oracle.query(g, s, t, 0.5, L, seed, cfg, want_u=True, want_q=True)
+    u = out["u"][0].astype(np.float64)
+    z = oracle.probe_vector(g.n, seed, 0)[0].astype(np.float64)
+    phi = float(z @ exact.series_h(g.row_ptr, g.col_idx, g.n, s, t, L))
+    assert abs(u.mean() - phi) < 5 * u.std() / math.sqrt(R)
+    # Q_R is unbiased for phi^2 (Lemma 3.4); its spread is Eq. step1's variance
+    var_q = 4 / R * phi**2 * u.var() + 2 / (R * (R - 1)) * u.var() ** 2
+    assert abs(out["q"][0] - phi**2) < 6 * math.sqrt(var_q) + 1e-12
+
+
+def test_L0_replicas_are_deterministic(oracle_lib, tiny_graph):
+    g = tiny_graph
+    s, t, seed = 4, 90, 77
+    cfg = oracle.budget_cfg(mode=oracle.MODE_FIXED, B=3, G=1, R=7)
+    out = oracle.query(g, s, t, 0.3, 0, seed, cfg, want_u=True, want_q=True)
+    d = g.degrees
+    for k in range(3):
+        z = oracle.probe_vector(g.n, seed, k)[0]
+        u0 = np.float32(np.float32(z[s]) / np.float32(d[s])) - np.float32(np.float32(z[t]) / np.float32(d[t]))
+        assert np.all(out["u"][k] == u0)
+        assert out["q"][k] == pytest.approx(float(u0) ** 2, rel=1e-12, abs=1e-300)
+
+
+def test_per_replica_bound_lemma_3_6(oracle_lib, tiny_graph):
+    g = tiny_graph
+    L = 32
+    cfg = oracle.budget_cfg(mode=oracle.MODE_FIXED, B=20, G=1, R=64)
+    out = oracle.query(g, 10, 20, 0.2, L, 5, cfg, want_u=True)
+    assert np.abs(out["u"]).max() <= 2 * (L + 1) / g.d_min
+
+
+def test_mean_of_estimates_is_unbiased(oracle_lib):
+    g = barabasi_albert(60, 2, 7)
+    s, t, L = 3, 40, 6
+    want = exact.series_beta(g.row_ptr, g.col_idx, g.n, s, t, L)
+    cfg = oracle.budget_cfg(mode=oracle.MODE_FIXED, B=40, G=1, R=8)
+    seeds = query_seeds(300, 3)
+    beta, _, st = oracle.query_many(g, np.full(300, s), np.full(300, t), 0.5, L, seeds, cfg)
+    assert np.all(st == 0)
+    assert abs(beta.mean() - want) < 5 * beta.std() / math.sqrt(beta.size)
+
+
+def test_theory_budget_golden(oracle_lib):
+    g = complete_graph(10)
+    for row in _read_rows("budget_theory.txt"):
+        eps, delta, L, s, t = float(row[1]), float(row[2]), int(row[3]), int(row[4]), int(row[5])
+        B, G, K, R = (int(x) for x in row[6:10])
+        got = oracle.budget(g, s, t, eps, L, 1, oracle.budget_cfg(mode=oracle.MODE_THEORY, delta=delta))
+        assert (got["B"], got["G"], got["K"], got["R"]) == (B, G, K, R)
+
+
+def test_scaled_and_fixed_budgets(oracle_lib):
+    g = complete_graph(10)
+    got = oracle.budget(g, 0, 1, 0.1, 4, 1, oracle.budget_cfg(mode=oracle.MODE_SCALED, c_B=0.01, c_R=0.1, R_max=64))
+    assert got["B"] == 448 and got["G"] == 37 and got["R"] == 64  # ceil(84.2) clamped to R_max
+    got = oracle.budget(g, 0, 1, 0.1, 4, 1, oracle.budget_cfg(mode=oracle.MODE_FIXED, B=3, G=5, R=9))
+    assert (got["B"], got["G"], got["K"], got["R"]) == (3, 5, 15, 9)
+
+
+def test_pilot_budget_shape(oracle_lib, tiny_graph):
+    got = oracle.budget(tiny_graph, 3, 77, 0.2, 32, 12345)
+    assert got["B"] == 25 and got["G"] == 37 and got["K"] == 925
+    assert got["R"] % 32 == 0 and 32 <= got["R"] <= 4096
+    d = tiny_graph.degrees
+    theta0 = 0.125 * (1 - 0.1) * (1 / d[3] + 1 / d[77]) ** 2
+    assert got["theta_hat"] >= theta0
+    assert got["R"] >= 4 * got["sigma2_hat"] / got["theta_hat"]
+
+
+def test_same_node_and_bad_arguments(oracle_lib, tiny_graph):
+    assert oracle.query(tiny_graph, 7, 7, 0.2, 32, 1)["beta"] == 0.0
+    for args in ((0, 1, 0.0, 32), (0, 1, 1.0, 32), (0, 200, 0.2, 32), (-1, 1, 0.2, 32), (0, 1, 0.2, -1)):
+        with pytest.raises(ValueError):
+            oracle.query(tiny_graph, args[0], args[1], args[2], args[3], 1)
+
+
+def test_default_seed_depends_on_query(oracle_lib):
+    a = oracle.default_seed(1, 3, 4, 0.1, 200)
+    assert a == oracle.default_seed(1, 3, 4, 0.1, 200)
+    others = {oracle.default_seed(1, 4, 3, 0.1, 200), oracle.default_seed(2, 3, 4, 0.1, 200),
+              oracle.default_seed(1, 3, 4, 0.2, 200), oracle.default_seed(1, 3, 4, 0.1, 201)}
+    assert a not in others and len(others) == 4
+
+
+def test_pilot_accuracy_problem_1(oracle_lib, tiny_graph):
+    """>= 95% of queries within eps of the exact beta (Problem 1, Theorem 3.8's target)."""
+    g = tiny_graph
+    ex = exact.exact_beta_matrix(g.row_ptr, g.col_idx, g.n)
+    s, t = uniform_pairs(g.n, 32, 100)
+    seeds = query_seeds(32, 200)
+    beta, _, st = oracle.query_many(g, s, t, 0.2, 32, seeds)
+    assert np.all(st == 0)
+    rel = np.abs(beta - ex[s, t]) / ex[s, t]
+    assert (rel <= 0.2).mean() >= 0.95
