@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""ProbeWalk bench: batched queries/s on one GB300 (and N GPUs by query sharding).
+
+One step = one batch of the workload's queries through the whole hot path
+(budget, pilot, walks, U-statistic, median-of-means), all walks of all
+queries in one persistent launch.  `value` is timed with CUDA events on the
+launch stream with inputs resident in HBM (pw_query_batch_device); `e2e` is
+the same batch through the host-array entry point (pw_query_batch), pinned
+staging, host-to-device and device-to-host copies included.  L2 is flushed
+(256 MiB write) between timed steps, outside the timed events.
+
+--impl reference times the CPU oracle (the plain serial walker) on the box's
+host cores on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "queries/s at eps=0.1 (batched server vs 1-per-launch), walk-steps/s, p99 latency"
+
+WORKLOADS = {
+    "ba-1e5": dict(graph="ba-1e5", desc="Barabasi-Albert n=100000 m=5 (seed 1), int32 CSR", queries=1000, L=200,
+                   eps=0.1, pair_seed=101, seed_seed=1001),
+    "tiny-er200": dict(graph="tiny-er200", desc="Erdos-Renyi G(200, 8/199) + cycle (seed 0)", queries=64, L=32,
+                       eps=0.2, pair_seed=100, seed_seed=200),
+}
+
+SECTOR_BYTES = 32  # one 16-byte neighbour record per transition lives in one 32-byte sector
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p.get("hbm_gbs", 6800.0), "measured"
+    except OSError:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload_inputs(wl: dict, rank: int):
+    from pw_inputs import query_seeds, uniform_pairs, workload_graph
+
+    host = workload_graph(wl["graph"])
+    s, t = uniform_pairs(host.n, wl["queries"], wl["pair_seed"] + 7919 * rank)
+    seeds = query_seeds(wl["queries"], wl["seed_seed"] + 7919 * rank)
+    return host, s, t, seeds
+
+
+def cpu_oracle_sample(host, s, t, seeds, wl, count: int):
+    import oracle
+
+    oracle.build()
+    threads = oracle.max_threads()
+    count = min(count, s.size)
+    t0 = time.perf_counter()
+    beta, _, st = oracle.query_many(host, s[:count], t[:count], wl["eps"], wl["L"], seeds[:count], threads=threads)
+    dt = time.perf_counter() - t0
+    assert np.all(st == 0)
+    return count / dt, dt, threads, count
+
+
+def run_reference(args, wl, world, rank):
+    """CPU oracle arm: each step runs one query per host core, in parallel."""
+    if rank != 0:
+        return
+    host, s, t, seeds = workload_inputs(wl, 0)
+    import oracle
+
+    oracle.build()
+    threads = oracle.max_threads()
+    per_step = min(threads, s.size) if wl["queries"] > 64 else s.size
+    times = []
+    for i in range(args.warmup + args.steps):
+        lo = (i * per_step) % s.size
+        idx = np.arange(lo, lo + per_step) % s.size
+        t0 = time.perf_counter()
+        _, _, st = oracle.query_many(host, s[idx], t[idx], wl["eps"], wl["L"], seeds[idx], threads=threads)
+        dt = time.perf_counter() - t0
+        assert np.all(st == 0)
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = per_step * len(times) / total
+    sample = f"{per_step} queries of the {wl['queries']}-query batch per step, one OpenMP thread per query"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}; {wl['queries']} uniform pairs; L={wl['L']}; "
+                                   f"eps={wl['eps']}; delta=0.01; PILOT budget", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, wl, world, rank, local):
+    import torch
+
+    from paper_2512_05460_gb300 import build as pwbuild
+
+    pwbuild.build()
+    from paper_2512_05460_gb300 import probewalk as pw
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    host, s, t, seeds = workload_inputs(wl, rank)
+    nq = s.size
+    eps = np.full(nq, wl["eps"])
+    L = np.full(nq, wl["L"], np.int32)
+    g = pw.Graph(host.row_ptr, host.col_idx, device=local)
+    params = pw.make_params(c_B=args.c_B) if args.c_B else None
+    d_s = torch.from_numpy(s).to(dev)
+    d_t = torch.from_numpy(t).to(dev)
+    d_eps = torch.from_numpy(eps).to(dev)
+    d_L = torch.from_numpy(L).to(dev)
+    d_seed = torch.from_numpy(seeds.view(np.int64)).to(dev)
+    d_beta = torch.empty(nq, dtype=torch.float64, device=dev)
+    d_status = torch.empty(nq, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        pw.pw_query_batch_device(g.handle, nq, d_s, d_t, d_eps, d_L, d_seed, d_beta, d_status, params, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            flush.fill_(i & 0xFF)
+            step()
+    stream.synchronize()
+    assert int(d_status.abs().sum()) == 0, "query errors in warm-up"
+
+    # ---- timed region: device-resident inputs --------------------------------
+    sampler = ClockSampler(local)
+    pw.pw_profile(g.handle, enable=True, reset=True)
+    pw.pw_launch_count(reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_((i + 1) & 0xFF)
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    launches = pw.pw_launch_count(reset=True)
+    prof = pw.pw_profile(g.handle, enable=False, reset=True)
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = max_over_ranks(world, sum(step_ms), dev)
+    beta = d_beta.cpu().numpy()
+    assert int(d_status.abs().sum()) == 0 and np.all(np.isfinite(beta))
+    value = world * nq * args.steps / (total_ms / 1000.0)
+    transitions_per_step = prof["transitions"] / max(1, args.steps)
+    walk_ms_avg = prof["walk_ms"] / max(1, prof["walk_launches"])
+    walk_steps_per_s = world * (prof["transitions"] + prof["pilot_transitions"]) / (total_ms / 1000.0)
+
+    # ---- end to end through the host-array entry point -----------------------
+    for _ in range(1):
+        pw.pw_query_batch(g.handle, s, t, eps, L, seeds, params)
+    e2e_times = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b2, st2 = pw.pw_query_batch(g.handle, s, t, eps, L, seeds, params)
+        e2e_times.append(time.perf_counter() - t0)
+        assert np.all(st2 == 0)
+    assert np.array_equal(b2, beta), "host and device entry points disagree"
+    e2e_total = max_over_ranks(world, sum(e2e_times), dev)
+    e2e_value = world * nq * args.steps / e2e_total
+
+    # ---- one query per launch (the plain form), on a prefix of the batch ------
+    plain_n = min(args.plain, nq)
+    lat = []
+    for i in range(plain_n):
+        t0 = time.perf_counter()
+        pw.pw_query(g.handle, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i]), params)
+        lat.append(time.perf_counter() - t0)
+    plain_qps = plain_n / sum(lat) if lat else None
+
+    # ---- roofline of the walk kernel -----------------------------------------
+    hbm_peak, peak_kind = load_peaks()
+    walk_bytes = transitions_per_step * SECTOR_BYTES
+    achieved = walk_bytes / (walk_ms_avg / 1000.0) / 1e9 if walk_ms_avg > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "kernel": "walk_kernel",
+                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": walk_bytes,
+                "bytes_model": "32 B (one sector holding the 16 B neighbour record) per walk transition",
+                "walk_ms_per_launch": walk_ms_avg}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        qps, dt, threads, cnt = cpu_oracle_sample(host, s, t, seeds, wl, args.cpu_queries or os.cpu_count())
+        cpu = {"value": qps, "unit": "queries/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {cnt} queries of the batch, one OpenMP thread per query, {dt:.1f} s"}
+
+    if rank == 0:
+        lat_ms = sorted(1000 * x for x in lat)
+
+        def pct(p):
+            return lat_ms[min(len(lat_ms) - 1, int(round(p / 100 * (len(lat_ms) - 1))))] if lat_ms else None
+
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}; {nq} uniform pairs per GPU; L={wl['L']}; "
+                                   f"eps={wl['eps']}; delta=0.01; PILOT budget c_B={args.c_B or 1.0}",
+                       "queries_per_gpu": nq, "L": wl["L"], "eps": wl["eps"],
+                       "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
+                       "parallelism": f"query sharding x{world}"},
+            "walk_steps_per_s": walk_steps_per_s,
+            "transitions_per_step": transitions_per_step,
+            "plain_queries_per_s": plain_qps, "plain_sample": plain_n,
+            "batched_over_plain": (value / world) / plain_qps if plain_qps else None,
+            "latency_ms": {"plain_p50": pct(50), "plain_p99": pct(99), "batch_step": total_ms / args.steps},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": nq * 36,
+                    "d2h_bytes_per_step": nq * 12},
+            "gpu_launches": launches,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ba-1e5", choices=sorted(WORKLOADS))
+    ap.add_argument("--plain", type=int, default=64, help="queries timed in the one-query-per-launch form")
+    ap.add_argument("--c_B", type=float, default=0.0)
+    ap.add_argument("--cpu-queries", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    wl = WORKLOADS[args.workload]
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, wl, world, rank)
+    else:
+        run_ours(args, wl, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * probewalk.h — C ABI of the GB300 ProbeWalk library (libprobewalk.so).
+ *
+ * ProbeWalk (arXiv 2512.05460) estimates the squared biharmonic distance
+ *     beta(s,t) = || L^+ (e_s - e_t) ||^2                  (Definition 2.1, Eq. exact)
+ * of two nodes of an undirected graph to a relative error eps (Problem 1) by
+ * Algorithm 1: for K = B*G Paired-Sign Probes z^(k) (Definition 3.1, generated
+ * statelessly as in Section 3.3) it runs R independent pairs of length-L random
+ * walks from s and t, forms U_p = sum_i z_{X_i}/d_{X_i} - sum_i z_{~X_i}/d_{~X_i}
+ * (Eq. hatphi-def), the U-statistic Q_R = (S1^2 - S2) / (R(R-1)) (Eq. Q-Ustat),
+ * and returns the median of the G block means of B probes each
+ * (Eq. final-estimator).  The returned value estimates the truncated
+ * distance beta^(L) (Lemma 2.3), which is within eps*beta/2 of beta when L is
+ * chosen by Eq. uni_l / Theorem 3.8.
+ *
+ * Conventions for every function:
+ *   - No exception crosses this boundary.  Each function returns a pw_status;
+ *     on failure pw_last_error() returns a message for the calling thread.
+ *   - "host" pointers are ordinary CPU memory owned by the caller, read or
+ *     written only during the call.  "device" pointers are CUDA global memory
+ *     on the graph's device, owned by the caller.
+ *   - The library owns the device copy of the graph and its scratch memory.
+ *   - All node ids are 0-based.  Integers are little-endian native types.
+ *   - A call that takes a stream (cudaStream_t passed as void*) is ordered on
+ *     that stream; host-pointer calls synchronise before returning.
+ *   - Calls on one pw_graph are serialised by an internal lock.
+ *   - Results depend only on (graph, s, t, eps, L, seed, params): a query gives
+ *     the same estimate alone or inside any batch.
+ */
+#ifndef PROBEWALK_H_
+#define PROBEWALK_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PW_OK = 0,
+  PW_PENDING = 1,        /* server ticket not finished yet */
+  PW_ERR_ARG = -1,       /* invalid argument (node id, eps, L, sizes, null pointer) */
+  PW_ERR_GRAPH = -2,     /* graph not sorted/simple/symmetric/connected, or an isolated node */
+  PW_ERR_NOMEM = -3,     /* device or host allocation failed, or admission capacity exceeded */
+  PW_ERR_CUDA = -4,      /* a CUDA runtime call failed (message in pw_last_error) */
+  PW_ERR_TIMEOUT = -5,   /* a bounded wait expired */
+  PW_ERR_CANCELLED = -6, /* server query cancelled or server shut down */
+  PW_ERR_FULL = -7       /* server queue full */
+} pw_status;
+
+/* Budget modes.  THEORY is Algorithm 1's parameter line (Eqs. B-value,
+ * G-value, R-value, K-value).  The paper's experiments do not state the K and
+ * R they used; SCALED scales THEORY's B and R by c_B and c_R; FIXED takes B, G,
+ * R as given; PILOT (default) keeps G, takes B = ceil(c_B / eps^2) and sets R
+ * from Lemma 3.7's sufficient condition R >= 4 sigma^2 / theta, with sigma^2 and
+ * theta estimated by a pilot of K0 probes x R0 replicas on reserved streams
+ * (theta floored by theta_0 = (1/8)(1 - eps/2)(1/d_s + 1/d_t)^2 from the proof of
+ * Theorem 3.8), rounded up to a multiple of 32 and clamped to [32, R_max]. */
+enum { PW_BUDGET_PILOT = 0, PW_BUDGET_THEORY = 1, PW_BUDGET_SCALED = 2, PW_BUDGET_FIXED = 3 };
+
+/* Parameters; an all-zero struct selects every default. */
+typedef struct pw_params {
+  double delta;            /* failure probability of Theorem 3.8; 0 -> 0.01 */
+  int32_t budget_mode;     /* PW_BUDGET_*; default PILOT */
+  int32_t pilot_K0;        /* PILOT probes; 0 -> 64 */
+  int32_t pilot_R0;        /* PILOT replicas per probe, 2..32; 0 -> 32 */
+  int32_t reserved0;
+  double c_B;              /* 0 -> 1.0 */
+  double c_R;              /* 0 -> 1.0 */
+  uint64_t B, G, R;        /* FIXED mode values (B >= 1, G >= 1, R >= 2) */
+  uint64_t R_max;          /* PILOT / SCALED clamp; 0 -> 4096 */
+  uint64_t seed;           /* global seed for queries that pass no seed */
+  int32_t tiles_per_claim; /* walk-kernel tiles claimed per work-queue pop; 0 -> autotuned */
+  int32_t block_threads;   /* walk-kernel block size; 0 -> autotuned */
+} pw_params;
+
+typedef struct pw_graph pw_graph;
+typedef struct pw_server pw_server;
+
+/* ---- graph ---------------------------------------------------------------
+ * pw_graph_load: validate an undirected simple graph given as CSR and upload
+ * it to CUDA device `device`.  row_ptr[0..n] (host) are row offsets with
+ * row_ptr[0] = 0 and row_ptr[n] = nnz; col_idx[0..nnz) (host) are neighbour
+ * ids, each row strictly increasing (so no duplicates), no self-loops, every
+ * edge present in both directions, every node of degree >= 1, the graph
+ * connected (Section 2.1).  Requires 2 <= n < 2^31 and nnz < 2^31.  The arrays
+ * are copied; the caller keeps ownership.  flags: bit 0 skips the O(n + m)
+ * connectivity check.  Returns PW_ERR_GRAPH if a check fails.
+ * On success *out holds a handle to free with pw_graph_free. */
+pw_status pw_graph_load(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz,
+                        int32_t device, uint32_t flags, pw_graph** out);
+/* Same with 32-bit row offsets. */
+pw_status pw_graph_load32(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t nnz,
+                          int32_t device, uint32_t flags, pw_graph** out);
+void pw_graph_free(pw_graph* g);
+/* Graph facts: n, nnz (directed entries), minimum and maximum degree,
+ * bipartite flag (1 when 2-colourable: the paper assumes non-bipartite,
+ * Section 2.1; estimates then target beta^(L) only).  Any output may be NULL. */
+pw_status pw_graph_info(const pw_graph* g, int64_t* n, int64_t* nnz, int32_t* d_min, int32_t* d_max,
+                        int32_t* bipartite);
+
+/* ---- budget ----------------------------------------------------------------
+ * Budget of one query (Algorithm 1, line 1): writes B, G, K = B*G, R.  In
+ * PILOT mode this runs the pilot walks on the GPU.  seed: host pointer to the
+ * query's 64-bit seed, or NULL for pw_default_seed(params->seed, s, t, eps, L).
+ * s == t gives all zeros. */
+pw_status pw_budget(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
+                    const pw_params* params, uint64_t* B, uint64_t* G, uint64_t* K, uint64_t* R);
+
+/* Default per-query seed: Philox4x32-10 keyed by (params seed XOR bits of eps)
+ * over the counter (s, t, L, 0x5EED); first two output words. */
+uint64_t pw_default_seed(uint64_t global_seed, int64_t s, int64_t t, double eps, int32_t L);
+
+/* ---- queries ---------------------------------------------------------------
+ * pw_query: one query, one pipeline of launches (the "one query per launch"
+ * form).  eps in (0,1), L >= 0, 0 <= s,t < n.  *beta_hat (host) receives the
+ * estimate of beta^(L)(s,t); it may be negative for tiny distances (the
+ * U-statistic is unbiased, not positive).  s == t returns exactly 0. */
+pw_status pw_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
+                   const pw_params* params, double* beta_hat);
+
+/* pw_query_batch: `count` independent queries (host arrays of length count;
+ * seeds may be NULL for default seeds).  All walks of all queries run in one
+ * persistent launch.  beta_hat and per_query_status (host) receive the
+ * results; the return value is PW_OK when the batch ran, even if some queries
+ * have a per-query error status.  count == 0 is a no-op. */
+pw_status pw_query_batch(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
+                         const int32_t* L, const uint64_t* seeds, const pw_params* params, double* beta_hat,
+                         int32_t* per_query_status);
+
+/* pw_query_batch_device: as pw_query_batch with every array in device memory
+ * and the work ordered on `stream` (a cudaStream_t, NULL for the legacy default
+ * stream).  The call returns after the launches are enqueued; it synchronises
+ * `stream` once, after the pilot, to size its scratch memory. */
+pw_status pw_query_batch_device(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t,
+                                const double* d_eps, const int32_t* d_L, const uint64_t* d_seeds,
+                                const pw_params* params, double* d_beta_hat, int32_t* d_status, void* stream);
+
+/* ---- server (continuous batching) ----------------------------------------
+ * A server keeps the graph and the per-query accumulators on the device and
+ * runs a persistent kernel fed by a device work queue.  Queries are admitted
+ * while their accumulator memory (16 bytes per walk tile + 8 bytes per probe)
+ * fits in accum_bytes; later ones wait in a host queue.  submit never blocks
+ * on the GPU; poll returns PW_PENDING until the ticket is done. */
+pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_bytes, pw_server** out);
+pw_status pw_server_submit(pw_server* srv, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
+                           uint64_t* ticket);
+pw_status pw_server_poll(pw_server* srv, uint64_t ticket, double* beta_hat);
+/* Wait up to timeout_ms for every submitted ticket; PW_ERR_TIMEOUT otherwise. */
+pw_status pw_server_drain(pw_server* srv, int64_t timeout_ms);
+pw_status pw_server_destroy(pw_server* srv);
+
+/* ---- debug / parity (tests) -------------------------------------------------
+ * pw_debug_philox: Philox4x32-10 evaluated on the device (host arrays:
+ * ctr[4], key[2], out[4]). */
+pw_status pw_debug_philox(pw_graph* g, const uint32_t* ctr, const uint32_t* key, uint32_t* out);
+/* pw_debug_probe: probe entries z^(k)_v for every node v (host int8 array of
+ * n) of probe k under stream tag `tag` (3 main, 4 pilot) of the query keyed by
+ * seed; returns the parity parameter r in *r (host, may be NULL). */
+pw_status pw_debug_probe(pw_graph* g, uint64_t seed, uint32_t k, uint32_t tag, int8_t* z, int32_t* r);
+/* pw_debug_walk: trajectory X_0..X_L (host int64 array of L+1) of walk
+ * `walk_id` under stream tag `tag` (1 main, 2 pilot). */
+pw_status pw_debug_walk(pw_graph* g, int64_t start, int32_t L, uint64_t seed, uint64_t walk_id, uint32_t tag,
+                        int64_t* trajectory);
+/* pw_debug_query: pw_query that also returns (host arrays, each may be NULL)
+ * budget[4] = (B, G, K, R), pilot[3] = (sigma2_hat, q_bar, theta_hat), q[K]
+ * (Q_R per probe), u[K*R] (U_p, probe-major) and visits[n] (uint32 visit
+ * counts of all main walks, X_0 included).  q_cap and u_cap are the capacities
+ * of q and u in elements; PW_ERR_ARG if too small. */
+pw_status pw_debug_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
+                         const pw_params* params, double* beta_hat, uint64_t* budget, double* pilot, double* q,
+                         int64_t q_cap, float* u, int64_t u_cap, uint32_t* visits);
+/* pw_debug_batch_probe_q: run pw_query_batch and also copy out Q_R of
+ * selected probes (host arrays of length n_sel: query index, probe index ->
+ * q_sel), and the (K, R) of every query (host uint64 [count][2]). */
+pw_status pw_debug_batch_probe_q(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t,
+                                 const double* eps, const int32_t* L, const uint64_t* seeds,
+                                 const pw_params* params, double* beta_hat, int32_t* per_query_status,
+                                 uint64_t* KR, int64_t n_sel, const int64_t* sel_query, const int64_t* sel_probe,
+                                 double* q_sel);
+
+/* ---- instrumentation -------------------------------------------------------
+ * When enabled, batch calls on `g` record CUDA events on their launch stream
+ * around the walk kernel and the finishing kernels.  pw_profile with out !=
+ * NULL waits for the recorded events and writes the accumulated figures;
+ * reset != 0 clears them afterwards.  transitions = sum over queries of
+ * 2 K R L, the walk steps Algorithm 1 performs (pilot steps counted apart). */
+typedef struct pw_profile_stats {
+  double walk_ms;              /* main walk-kernel launches, summed */
+  double pilot_ms;             /* pilot walk-kernel launches, summed */
+  double finish_ms;            /* per-probe U-statistic + median-of-means kernels */
+  uint64_t walk_launches;
+  uint64_t transitions;
+  uint64_t pilot_transitions;
+  uint64_t queries;
+} pw_profile_stats;
+pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stats* out);
+
+/* Kernel launches issued by this thread since the last call (instrumentation). */
+uint64_t pw_launch_count(int reset);
+/* Message describing the last error on this thread ("" if none). */
+const char* pw_last_error(void);
+/* Library version string. */
+const char* pw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PROBEWALK_H_ */

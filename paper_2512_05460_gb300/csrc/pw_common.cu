@@ -1,0 +1,138 @@
+// Errors, instrumentation, memory helpers and budget defaults.
+#include <math.h>
+#include <stdio.h>
+
+#include "pw_device.cuh"
+#include "pw_internal.h"
+
+namespace pw {
+
+static thread_local std::string g_last_error;
+static thread_local uint64_t g_launches = 0;
+
+pw_status set_error(pw_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+pw_status cuda_error(cudaError_t err, const char* what) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s", (int)err, cudaGetErrorString(err), what);
+  g_last_error = buf;
+  return PW_ERR_CUDA;
+}
+
+void count_launch() { ++g_launches; }
+
+pw_status ensure_buffer(DeviceBuffer& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return PW_OK;
+  if (b.ptr) cudaFree(b.ptr);
+  b.ptr = nullptr;
+  b.bytes = 0;
+  size_t want = bytes + bytes / 4;
+  cudaError_t e = cudaMalloc(&b.ptr, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&b.ptr, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b.ptr = nullptr;
+      char buf[128];
+      snprintf(buf, sizeof buf, "cudaMalloc of %zu bytes failed", bytes);
+      return set_error(PW_ERR_NOMEM, buf);
+    }
+    want = bytes;
+  }
+  b.bytes = want;
+  return PW_OK;
+}
+
+void free_buffer(DeviceBuffer& b) {
+  if (b.ptr) cudaFree(b.ptr);
+  b.ptr = nullptr;
+  b.bytes = 0;
+}
+
+pw_status ensure_host_staging(Workspace& ws, size_t bytes) {
+  if (ws.host_staging_bytes >= bytes) return PW_OK;
+  if (ws.host_staging) cudaFreeHost(ws.host_staging);
+  ws.host_staging = nullptr;
+  ws.host_staging_bytes = 0;
+  size_t want = bytes + bytes / 4 + 4096;
+  PW_CUDA_TRY(cudaMallocHost(&ws.host_staging, want));
+  ws.host_staging_bytes = want;
+  return PW_OK;
+}
+
+void free_workspace(Workspace& ws) {
+  free_buffer(ws.plans);
+  free_buffer(ws.pilot_plans);
+  free_buffer(ws.tile_prefix);
+  free_buffer(ws.pilot_u);
+  free_buffer(ws.u);
+  free_buffer(ws.q);
+  free_buffer(ws.totals);
+  free_buffer(ws.counters);
+  free_buffer(ws.queries);
+  free_buffer(ws.results);
+  if (ws.host_totals) cudaFreeHost(ws.host_totals);
+  ws.host_totals = nullptr;
+  if (ws.host_staging) cudaFreeHost(ws.host_staging);
+  ws.host_staging = nullptr;
+  ws.host_staging_bytes = 0;
+  if (ws.last_use) cudaEventDestroy(ws.last_use);
+  ws.last_use = nullptr;
+}
+
+pw_status resolve_budget(const pw_params* params, const pw_graph* g, BudgetArgs* out, double* delta_out) {
+  pw_params p{};
+  if (params) p = *params;
+  double delta = p.delta > 0 ? p.delta : 0.01;
+  if (!(delta > 0.0 && delta < 1.0)) return set_error(PW_ERR_ARG, "delta must lie in (0, 1)");
+  BudgetArgs a{};
+  a.mode = p.budget_mode;
+  if (a.mode < PW_BUDGET_PILOT || a.mode > PW_BUDGET_FIXED) return set_error(PW_ERR_ARG, "unknown budget_mode");
+  a.K0 = p.pilot_K0 > 0 ? p.pilot_K0 : 64;
+  a.R0 = p.pilot_R0 > 1 ? p.pilot_R0 : 32;
+  if (a.R0 > 32) return set_error(PW_ERR_ARG, "pilot_R0 must be at most 32");
+  // G = ceil(8 ln(1/delta)) with the same tolerant ceiling as B and R.
+  double gx = ceil(8.0 * log(1.0 / delta) * (1.0 - 1e-12));
+  a.G = gx < 1.0 ? 1u : (uint32_t)gx;
+  a.c_B = p.c_B > 0 ? p.c_B : 1.0;
+  a.c_R = p.c_R > 0 ? p.c_R : 1.0;
+  a.R_max = p.R_max ? p.R_max : 4096;
+  if (a.mode == PW_BUDGET_FIXED) {
+    if (p.B < 1 || p.G < 1 || p.R < 2) return set_error(PW_ERR_ARG, "FIXED budget needs B >= 1, G >= 1, R >= 2");
+    if (p.G > 4096) return set_error(PW_ERR_ARG, "G above 4096");
+    a.B_fixed = p.B;
+    a.G = (uint32_t)p.G;
+    a.R_fixed = p.R;
+  }
+  if (a.G > 4096) return set_error(PW_ERR_ARG, "delta too small: G above 4096");
+  a.global_seed = p.seed;
+  a.d_min = g ? g->d_min : 1;
+  *out = a;
+  if (delta_out) *delta_out = delta;
+  return PW_OK;
+}
+
+}  // namespace pw
+
+extern "C" {
+
+const char* pw_last_error(void) { return pw::g_last_error.c_str(); }
+
+uint64_t pw_launch_count(int reset) {
+  uint64_t v = pw::g_launches;
+  if (reset) pw::g_launches = 0;
+  return v;
+}
+
+const char* pw_version(void) { return "probewalk-gb300 0.1 (sm_103a)"; }
+
+uint64_t pw_default_seed(uint64_t global_seed, int64_t s, int64_t t, double eps, int32_t L) {
+  return pw::default_seed(global_seed, s, t, eps, L);
+}
+
+}  // extern "C"

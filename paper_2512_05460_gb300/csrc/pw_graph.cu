@@ -1,0 +1,273 @@
+// Graph loading (validation, neighbour-record layout, upload) and the small
+// debug kernels (Philox, probe vector, single trajectory).
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pw_device.cuh"
+#include "pw_internal.h"
+
+namespace pw {
+
+// rec[e] = {u, row_start(u), deg(u), bits(1/deg(u))} for every CSR entry e; node[v] likewise for v.
+__global__ void build_records_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                     int64_t n, int64_t nnz, int4* __restrict__ rec, int4* __restrict__ node) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz + n; e += stride) {
+    const int32_t u = e < nnz ? col[e] : (int32_t)(e - nnz);
+    const int32_t start = row_ptr[u];
+    const int32_t d = row_ptr[u + 1] - start;
+    const float inv = __fdiv_rn(1.0f, (float)d);
+    const int4 r = make_int4(u, start, d, (int)__float_as_uint(inv));
+    if (e < nnz)
+      rec[e] = r;
+    else
+      node[e - nnz] = r;
+  }
+}
+
+__global__ void debug_philox_kernel(uint4 ctr, uint2 key, uint4* out) {
+  const Philox4 o = philox4x32_10(ctr.x, ctr.y, ctr.z, ctr.w, key.x, key.y);
+  *out = make_uint4(o.x, o.y, o.z, o.w);
+}
+
+__global__ void debug_probe_kernel(uint32_t n, uint64_t seed, uint32_t k, uint32_t tag, int8_t* z, int32_t* r) {
+  const Probe P = make_probe(n, seed, k, tag);
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    z[v] = (int8_t)probe_z(P, v);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *r = (int32_t)(n - P.n_active);
+}
+
+// One trajectory with the walk kernel's step rule: step i draws word (i & 3) of
+// the Philox block (walk lo, walk hi, i >> 2, tag) and moves to neighbour
+// floor(word * d / 2^32).
+__global__ void debug_walk_kernel(const int4* __restrict__ rec, const int4* __restrict__ node, int32_t start,
+                                  int32_t L, uint64_t seed, uint64_t walk_id, uint32_t tag, int64_t* traj) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int4 cur = node[start];
+  traj[0] = cur.x;
+  for (int32_t i = 1; i <= L; ++i) {
+    const Philox4 o = philox_seeded(seed, (uint32_t)walk_id, (uint32_t)(walk_id >> 32), (uint32_t)i >> 2, tag);
+    const uint32_t w[4] = {o.x, o.y, o.z, o.w};
+    const uint32_t j = __umulhi(w[i & 3], (uint32_t)cur.z);
+    cur = rec[(uint32_t)cur.y + j];
+    traj[i] = cur.x;
+  }
+}
+
+static pw_status validate_csr(int64_t n, const int64_t* rp, const int32_t* col, int64_t nnz, uint32_t flags,
+                              int32_t* d_min, int32_t* d_max, int32_t* bipartite) {
+  if (rp[0] != 0 || rp[n] != nnz) return set_error(PW_ERR_GRAPH, "row_ptr must start at 0 and end at nnz");
+  int32_t dmn = INT32_MAX, dmx = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    const int64_t a = rp[v], b = rp[v + 1];
+    if (b < a || b > nnz) return set_error(PW_ERR_GRAPH, "row_ptr is not monotone within [0, nnz] at node " + std::to_string(v));
+    if (b == a) return set_error(PW_ERR_GRAPH, "isolated node " + std::to_string(v));
+    const int64_t d = b - a;
+    dmn = (int32_t)std::min<int64_t>(dmn, d);
+    dmx = (int32_t)std::max<int64_t>(dmx, d);
+    for (int64_t e = a; e < b; ++e) {
+      const int32_t u = col[e];
+      if (u < 0 || u >= n) return set_error(PW_ERR_GRAPH, "neighbour id out of range in row " + std::to_string(v));
+      if (u == v) return set_error(PW_ERR_GRAPH, "self-loop at node " + std::to_string(v));
+      if (e > a && col[e - 1] >= u)
+        return set_error(PW_ERR_GRAPH, "row " + std::to_string(v) + " is not strictly increasing");
+    }
+  }
+  // symmetry: (v,u) present implies (u,v) present
+  for (int64_t v = 0; v < n; ++v) {
+    for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
+      const int32_t u = col[e];
+      if (!std::binary_search(col + rp[u], col + rp[u + 1], (int32_t)v))
+        return set_error(PW_ERR_GRAPH, "edge (" + std::to_string(v) + "," + std::to_string(u) + ") has no reverse");
+    }
+  }
+  *d_min = dmn;
+  *d_max = dmx;
+  *bipartite = 0;
+  if (!(flags & 1u)) {
+    // breadth-first search from node 0: connectivity and 2-colouring
+    std::vector<int8_t> colour((size_t)n, -1);
+    std::vector<int32_t> queue;
+    queue.reserve((size_t)n);
+    colour[0] = 0;
+    queue.push_back(0);
+    bool two = true;
+    for (size_t head = 0; head < queue.size(); ++head) {
+      const int32_t v = queue[head];
+      for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
+        const int32_t u = col[e];
+        if (colour[u] < 0) {
+          colour[u] = (int8_t)(1 - colour[v]);
+          queue.push_back(u);
+        } else if (colour[u] == colour[v]) {
+          two = false;
+        }
+      }
+    }
+    if ((int64_t)queue.size() != n) return set_error(PW_ERR_GRAPH, "graph is not connected");
+    *bipartite = two ? 1 : 0;
+  }
+  return PW_OK;
+}
+
+static pw_status upload(pw_graph* g, const int64_t* rp64, const int32_t* col) {
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  PW_CUDA_TRY(cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device));
+  PW_CUDA_TRY(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+  std::vector<int32_t> rp32((size_t)g->n + 1);
+  for (int64_t i = 0; i <= g->n; ++i) rp32[(size_t)i] = (int32_t)rp64[i];
+  int32_t *d_rp = nullptr, *d_col = nullptr;
+  PW_CUDA_TRY(cudaMalloc(&d_rp, sizeof(int32_t) * (size_t)(g->n + 1)));
+  PW_CUDA_TRY(cudaMalloc(&d_col, sizeof(int32_t) * (size_t)g->nnz));
+  PW_CUDA_TRY(cudaMalloc(&g->d_rec, sizeof(int4) * (size_t)g->nnz));
+  PW_CUDA_TRY(cudaMalloc(&g->d_node, sizeof(int4) * (size_t)g->n));
+  PW_CUDA_TRY(cudaMemcpyAsync(d_rp, rp32.data(), sizeof(int32_t) * (size_t)(g->n + 1), cudaMemcpyHostToDevice,
+                              g->stream));
+  PW_CUDA_TRY(cudaMemcpyAsync(d_col, col, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyHostToDevice, g->stream));
+  const int threads = 256;
+  const int64_t work = g->nnz + g->n;
+  const int blocks = (int)std::min<int64_t>((work + threads - 1) / threads, (int64_t)g->sm_count * 32);
+  build_records_kernel<<<blocks, threads, 0, g->stream>>>(d_rp, d_col, g->n, g->nnz, g->d_rec, g->d_node);
+  count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  cudaFree(d_rp);
+  cudaFree(d_col);
+  PW_CUDA_TRY(cudaMallocHost(&g->ws.host_totals, sizeof(Totals)));
+  PW_CUDA_TRY(cudaEventCreateWithFlags(&g->ws.last_use, cudaEventDisableTiming));
+  return PW_OK;
+}
+
+static void destroy(pw_graph* g) {
+  if (!g) return;
+  cudaSetDevice(g->device);
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  free_workspace(g->ws);
+  for (auto& sp : g->prof.spans) {
+    cudaEventDestroy(sp.a);
+    cudaEventDestroy(sp.b);
+  }
+  for (cudaEvent_t e : g->prof.pool) cudaEventDestroy(e);
+  if (g->d_rec) cudaFree(g->d_rec);
+  if (g->d_node) cudaFree(g->d_node);
+  if (g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+}
+
+static pw_status load_common(int64_t n, const int64_t* rp, const int32_t* col, int64_t nnz, int32_t device,
+                             uint32_t flags, pw_graph** out) {
+  if (!out) return set_error(PW_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!rp || !col) return set_error(PW_ERR_ARG, "row_ptr/col_idx is NULL");
+  if (n < 2 || n >= (int64_t)1 << 31) return set_error(PW_ERR_ARG, "n must lie in [2, 2^31)");
+  if (nnz < 1 || nnz >= (int64_t)1 << 31) return set_error(PW_ERR_ARG, "nnz must lie in [1, 2^31)");
+  int32_t dmn = 0, dmx = 0, bip = 0;
+  pw_status st = validate_csr(n, rp, col, nnz, flags, &dmn, &dmx, &bip);
+  if (st != PW_OK) return st;
+  pw_graph* g = new (std::nothrow) pw_graph();
+  if (!g) return set_error(PW_ERR_NOMEM, "host allocation failed");
+  g->device = device;
+  g->n = n;
+  g->nnz = nnz;
+  g->d_min = dmn;
+  g->d_max = dmx;
+  g->bipartite = bip;
+  st = upload(g, rp, col);
+  if (st != PW_OK) {
+    destroy(g);
+    return st;
+  }
+  *out = g;
+  return PW_OK;
+}
+
+}  // namespace pw
+
+extern "C" {
+
+pw_status pw_graph_load(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz, int32_t device,
+                        uint32_t flags, pw_graph** out) {
+  return pw::load_common(n, row_ptr, col_idx, nnz, device, flags, out);
+}
+
+pw_status pw_graph_load32(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t nnz, int32_t device,
+                          uint32_t flags, pw_graph** out) {
+  if (!row_ptr || n < 2) return pw::set_error(PW_ERR_ARG, "row_ptr is NULL or n < 2");
+  std::vector<int64_t> rp((size_t)n + 1);
+  for (int32_t i = 0; i <= n; ++i) rp[(size_t)i] = row_ptr[i];
+  return pw::load_common(n, rp.data(), col_idx, nnz, device, flags, out);
+}
+
+void pw_graph_free(pw_graph* g) { pw::destroy(g); }
+
+pw_status pw_graph_info(const pw_graph* g, int64_t* n, int64_t* nnz, int32_t* d_min, int32_t* d_max,
+                        int32_t* bipartite) {
+  if (!g) return pw::set_error(PW_ERR_ARG, "graph is NULL");
+  if (n) *n = g->n;
+  if (nnz) *nnz = g->nnz;
+  if (d_min) *d_min = g->d_min;
+  if (d_max) *d_max = g->d_max;
+  if (bipartite) *bipartite = g->bipartite;
+  return PW_OK;
+}
+
+pw_status pw_debug_philox(pw_graph* g, const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  if (!g || !ctr || !key || !out) return pw::set_error(PW_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  pw::DeviceBuffer& b = g->ws.results;
+  pw_status st = pw::ensure_buffer(b, 64);
+  if (st != PW_OK) return st;
+  pw::debug_philox_kernel<<<1, 1, 0, g->stream>>>(make_uint4(ctr[0], ctr[1], ctr[2], ctr[3]),
+                                                   make_uint2(key[0], key[1]), (uint4*)b.ptr);
+  pw::count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  PW_CUDA_TRY(cudaMemcpyAsync(out, b.ptr, 16, cudaMemcpyDeviceToHost, g->stream));
+  PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return PW_OK;
+}
+
+pw_status pw_debug_probe(pw_graph* g, uint64_t seed, uint32_t k, uint32_t tag, int8_t* z, int32_t* r) {
+  if (!g || !z) return pw::set_error(PW_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  pw::DeviceBuffer& b = g->ws.results;
+  pw_status st = pw::ensure_buffer(b, (size_t)g->n + 64);
+  if (st != PW_OK) return st;
+  int32_t* d_r = (int32_t*)((char*)b.ptr + ((size_t)g->n + 15) / 16 * 16);
+  const int blocks = (int)std::min<int64_t>((g->n + 255) / 256, (int64_t)g->sm_count * 8);
+  pw::debug_probe_kernel<<<blocks, 256, 0, g->stream>>>((uint32_t)g->n, seed, k, tag, (int8_t*)b.ptr, d_r);
+  pw::count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  PW_CUDA_TRY(cudaMemcpyAsync(z, b.ptr, (size_t)g->n, cudaMemcpyDeviceToHost, g->stream));
+  int32_t rr = 0;
+  PW_CUDA_TRY(cudaMemcpyAsync(&rr, d_r, sizeof rr, cudaMemcpyDeviceToHost, g->stream));
+  PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (r) *r = rr;
+  return PW_OK;
+}
+
+pw_status pw_debug_walk(pw_graph* g, int64_t start, int32_t L, uint64_t seed, uint64_t walk_id, uint32_t tag,
+                        int64_t* trajectory) {
+  if (!g || !trajectory) return pw::set_error(PW_ERR_ARG, "NULL argument");
+  if (start < 0 || start >= g->n || L < 0) return pw::set_error(PW_ERR_ARG, "start or L out of range");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  pw::DeviceBuffer& b = g->ws.results;
+  pw_status st = pw::ensure_buffer(b, sizeof(int64_t) * ((size_t)L + 1));
+  if (st != PW_OK) return st;
+  pw::debug_walk_kernel<<<1, 32, 0, g->stream>>>(g->d_rec, g->d_node, (int32_t)start, L, seed, walk_id, tag,
+                                                 (int64_t*)b.ptr);
+  pw::count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  PW_CUDA_TRY(cudaMemcpyAsync(trajectory, b.ptr, sizeof(int64_t) * ((size_t)L + 1), cudaMemcpyDeviceToHost,
+                              g->stream));
+  PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return PW_OK;
+}
+
+}  // extern "C"

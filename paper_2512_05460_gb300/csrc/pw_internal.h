@@ -1,0 +1,121 @@
+// Internal types shared by the translation units of libprobewalk.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "probewalk.h"
+
+namespace pw {
+
+// Per-query plan, one per query of a batch, resident in device memory.
+struct QPlan {
+  uint64_t seed;
+  uint64_t tile_begin;   // first walk tile of this query (tiles are 32 replicas of one probe)
+  uint64_t u_begin;      // first U_p slot (probe-major, K*R slots)
+  uint64_t probe_begin;  // first Q slot (K slots)
+  int32_t s, t;
+  int32_t L;
+  int32_t status;        // pw_status of this query
+  uint32_t K, R, B, G;
+  uint32_t chunks;       // ceil(R / 32)
+  uint32_t pad0;
+  double eps;
+  double sigma2, qbar, theta;  // pilot diagnostics
+};
+
+// Totals written by the scan kernel.
+struct Totals {
+  unsigned long long tiles;
+  unsigned long long u_slots;
+  unsigned long long probes;
+  unsigned long long steps;  // sum of K * R * L (walk pairs times length)
+};
+
+struct ProfileState {
+  bool enabled = false;
+  struct Span {
+    cudaEvent_t a, b;
+    int kind;  // 0 main walk, 1 pilot walk, 2 finish
+  };
+  std::vector<Span> spans;
+  std::vector<cudaEvent_t> pool;
+  double walk_ms = 0, pilot_ms = 0, finish_ms = 0;
+  uint64_t walk_launches = 0, transitions = 0, pilot_transitions = 0, queries = 0;
+};
+
+// Budget inputs shared by all queries of a call (resolved defaults).
+struct BudgetArgs {
+  int32_t mode;
+  int32_t K0, R0;
+  uint32_t G;       // ceil(8 ln(1/delta)), evaluated on the host
+  double c_B, c_R;
+  uint64_t B_fixed, R_fixed;
+  uint64_t R_max;
+  uint64_t global_seed;
+  int32_t d_min;
+};
+
+struct DeviceBuffer {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct Workspace {
+  DeviceBuffer plans, pilot_plans, tile_prefix, pilot_u, u, q, totals, counters, queries, results;
+  Totals* host_totals = nullptr;  // pinned
+  void* host_staging = nullptr;   // pinned
+  size_t host_staging_bytes = 0;
+  cudaEvent_t last_use = nullptr;
+};
+
+}  // namespace pw
+
+struct pw_graph {
+  int device = 0;
+  int64_t n = 0, nnz = 0;
+  int32_t d_min = 0, d_max = 0, bipartite = 0;
+  int sm_count = 0;
+  int4* d_rec = nullptr;   // nnz neighbour records
+  int4* d_node = nullptr;  // n node records
+  cudaStream_t stream = nullptr;
+  std::mutex lock;
+  pw::Workspace ws;
+  pw::ProfileState prof;
+};
+
+namespace pw {
+
+pw_status set_error(pw_status st, const std::string& msg);
+pw_status cuda_error(cudaError_t err, const char* what);
+void count_launch();
+pw_status ensure_buffer(DeviceBuffer& b, size_t bytes);
+void free_buffer(DeviceBuffer& b);
+pw_status ensure_host_staging(Workspace& ws, size_t bytes);
+void free_workspace(Workspace& ws);
+
+// Resolve defaults; returns PW_ERR_ARG on invalid FIXED values.
+pw_status resolve_budget(const pw_params* params, const pw_graph* g, BudgetArgs* out, double* delta_out);
+
+// Run a batch whose query arrays are already on the device.  Writes beta and
+// status (device).  If debug_u / debug_q / debug_visits are non-null the
+// corresponding debug outputs are produced (device pointers sized by caller).
+struct DebugOut {
+  uint32_t* visits = nullptr;  // device, n counters of visits by the main walks
+  bool budget_only = false;    // stop after the budget (and pilot) stage
+};
+pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t, const double* d_eps,
+                    const int32_t* d_L, const uint64_t* d_seeds, const pw_params* params, double* d_beta,
+                    int32_t* d_status, cudaStream_t stream, DebugOut* dbg);
+
+}  // namespace pw
+
+#define PW_CUDA_TRY(expr)                                            \
+  do {                                                               \
+    cudaError_t _e = (expr);                                         \
+    if (_e != cudaSuccess) return pw::cuda_error(_e, #expr);         \
+  } while (0)

@@ -1,0 +1,780 @@
+// Query pipeline of Algorithm 1 on the device:
+//   budget (line 1) -> [pilot walks + pilot budget] -> tile/U/probe offsets ->
+//   persistent walk kernel (lines 2-11) -> per-probe U-statistic (lines 12-14)
+//   -> median of block means (lines 16-20).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pw_device.cuh"
+#include "pw_internal.h"
+
+namespace pw {
+
+constexpr int kWalkThreads = 256;
+
+__host__ __device__ __forceinline__ double ceil_tol(double x) { return ceil(x * (1.0 - 1e-12)); }
+
+// R of Eq. R-value before the ceiling.
+__device__ __forceinline__ double r_theory_raw(double eps, int32_t L, double d_min, double ds, double dt) {
+  const double inv = 1.0 / ds + 1.0 / dt;
+  return 128.0 * (double)(L + 1) * (double)(L + 1) / (d_min * d_min * (1.0 - eps / 2.0) * inv * inv);
+}
+
+// ---------------------------------------------------------------------------
+// Budget of every query (Algorithm 1 line 1).  PILOT queries get their pilot
+// plan here and their R in pilot_budget_kernel.
+// ---------------------------------------------------------------------------
+__global__ void budget_init_kernel(int64_t nq, const int64_t* __restrict__ qs, const int64_t* __restrict__ qt,
+                                   const double* __restrict__ qeps, const int32_t* __restrict__ qL,
+                                   const uint64_t* __restrict__ qseed, BudgetArgs A, int64_t n,
+                                   const int4* __restrict__ node, QPlan* __restrict__ plans,
+                                   QPlan* __restrict__ pilot) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  QPlan P;
+  memset(&P, 0, sizeof P);
+  const int64_t s = qs[q], t = qt[q];
+  const double eps = qeps[q];
+  const int32_t L = qL[q];
+  P.eps = eps;
+  P.L = L;
+  P.status = PW_OK;
+  QPlan PP = P;
+  if (s < 0 || s >= n || t < 0 || t >= n || !(eps > 0.0 && eps < 1.0) || L < 0) {
+    P.status = PW_ERR_ARG;
+  } else {
+    P.s = (int32_t)s;
+    P.t = (int32_t)t;
+    P.seed = qseed ? qseed[q] : default_seed(A.global_seed, s, t, eps, L);
+    if (s != t) {
+      const double ds = (double)node[s].z, dt = (double)node[t].z, dmin = (double)A.d_min;
+      double B = 0.0, R = 0.0;
+      const double G = (double)A.G;
+      switch (A.mode) {
+        case PW_BUDGET_THEORY:
+          B = ceil_tol(448.0 / (eps * eps));
+          R = ceil_tol(r_theory_raw(eps, L, dmin, ds, dt));
+          if (R < 2.0) R = 2.0;
+          break;
+        case PW_BUDGET_SCALED:
+          B = ceil_tol(A.c_B * 448.0 / (eps * eps));
+          if (B < 1.0) B = 1.0;
+          R = ceil_tol(A.c_R * r_theory_raw(eps, L, dmin, ds, dt));
+          if (R < 2.0) R = 2.0;
+          if (R > (double)A.R_max) R = (double)A.R_max;
+          break;
+        case PW_BUDGET_FIXED:
+          B = (double)A.B_fixed;
+          R = (double)A.R_fixed;
+          break;
+        default:  // PILOT
+          B = ceil_tol(A.c_B / (eps * eps));
+          if (B < 1.0) B = 1.0;
+          R = 0.0;
+          break;
+      }
+      if (B * G >= 4294967296.0 || R >= 4294967296.0) {
+        P.status = PW_ERR_ARG;  // budget beyond 2^32 probes or replicas
+      } else {
+        P.B = (uint32_t)B;
+        P.G = A.G;
+        P.K = P.B * P.G;
+        P.R = (uint32_t)R;
+        P.chunks = (P.R + 31u) / 32u;
+        if (A.mode == PW_BUDGET_PILOT) {
+          PP.s = P.s;
+          PP.t = P.t;
+          PP.seed = P.seed;
+          PP.K = (uint32_t)A.K0;
+          PP.R = (uint32_t)A.R0;
+          PP.chunks = 1;
+        }
+      }
+    }
+  }
+  if (P.status != PW_OK) {
+    P.K = 0;
+    P.R = 0;
+    P.chunks = 0;
+  }
+  plans[q] = P;
+  if (pilot) pilot[q] = PP;
+}
+
+// PILOT: R >= 4 sigma^2 / theta (Lemma 3.7) from the pilot replicas, in the
+// oracle's summation order (per probe over replicas, then over probes).
+__global__ void pilot_budget_kernel(int64_t nq, QPlan* __restrict__ plans, const QPlan* __restrict__ pilot,
+                                    const float* __restrict__ pilot_u, BudgetArgs A, const int4* __restrict__ node) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const QPlan PP = pilot[q];
+  if (PP.K == 0) return;
+  QPlan& P = plans[q];
+  const double R0 = (double)PP.R;
+  double sum_var = 0.0, sum_q = 0.0;
+  for (uint32_t k = 0; k < PP.K; ++k) {
+    const float* u = pilot_u + PP.u_begin + (uint64_t)k * PP.R;
+    double S1 = 0.0, S2 = 0.0;
+    for (uint32_t p = 0; p < PP.R; ++p) {
+      const double x = (double)u[p];
+      S1 = __dadd_rn(S1, x);
+      S2 = __dadd_rn(S2, __dmul_rn(x, x));
+    }
+    const double Q = __ddiv_rn(__dsub_rn(__dmul_rn(S1, S1), S2), __dmul_rn(R0, __dsub_rn(R0, 1.0)));
+    sum_var = __dadd_rn(sum_var, __ddiv_rn(__dsub_rn(S2, __ddiv_rn(__dmul_rn(S1, S1), R0)), __dsub_rn(R0, 1.0)));
+    sum_q = __dadd_rn(sum_q, Q);
+  }
+  const double sigma2 = sum_var / (double)PP.K;
+  const double q_bar = sum_q / (double)PP.K;
+  const double ds = (double)node[P.s].z, dt = (double)node[P.t].z;
+  const double inv = 1.0 / ds + 1.0 / dt;
+  const double theta0 = (1.0 / 8.0) * (1.0 - P.eps / 2.0) * inv * inv;
+  const double theta = q_bar > theta0 ? q_bar : theta0;
+  double R = ceil_tol(A.c_R * 4.0 * sigma2 / theta);
+  if (R < 2.0) R = 2.0;
+  R = 32.0 * ceil(R / 32.0);
+  if (R > (double)A.R_max) R = (double)A.R_max;
+  P.R = (uint32_t)R;
+  P.chunks = (P.R + 31u) / 32u;
+  P.sigma2 = sigma2;
+  P.qbar = q_bar;
+  P.theta = theta;
+}
+
+// Exclusive offsets of tiles (K*chunks), U slots (K*R) and probes (K); one
+// block.  prefix[0..nq] are tile offsets, prefix[nq+1..2nq+1] probe offsets.
+__global__ void scan_kernel(QPlan* __restrict__ plans, int64_t nq, unsigned long long* __restrict__ prefix,
+                            Totals* __restrict__ totals) {
+  __shared__ unsigned long long sh[3][1024];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t per = (nq + nt - 1) / nt;
+  const int64_t b0 = per * tid, b = b0 < nq ? b0 : nq, e = b + per < nq ? b + per : nq;
+  unsigned long long st = 0, su = 0, sp = 0, ss = 0;
+  for (int64_t q = b; q < e; ++q) {
+    const QPlan& P = plans[q];
+    st += (unsigned long long)P.K * P.chunks;
+    su += (unsigned long long)P.K * P.R;
+    sp += P.K;
+    ss += (unsigned long long)P.K * P.R * (unsigned long long)(P.L > 0 ? P.L : 0);
+  }
+  sh[0][tid] = st;
+  sh[1][tid] = su;
+  sh[2][tid] = sp;
+  __shared__ unsigned long long steps_sh[1024];
+  steps_sh[tid] = ss;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int i = 0; i < nt; ++i) {
+      const unsigned long long x0 = sh[0][i], x1 = sh[1][i], x2 = sh[2][i];
+      sh[0][i] = a0;
+      sh[1][i] = a1;
+      sh[2][i] = a2;
+      a0 += x0;
+      a1 += x1;
+      a2 += x2;
+      a3 += steps_sh[i];
+    }
+    totals->tiles = a0;
+    totals->u_slots = a1;
+    totals->probes = a2;
+    totals->steps = a3;
+    prefix[nq] = a0;
+    prefix[2 * nq + 1] = a2;
+  }
+  __syncthreads();
+  st = sh[0][tid];
+  su = sh[1][tid];
+  sp = sh[2][tid];
+  for (int64_t q = b; q < e; ++q) {
+    QPlan& P = plans[q];
+    P.tile_begin = st;
+    P.u_begin = su;
+    P.probe_begin = sp;
+    prefix[q] = st;
+    prefix[nq + 1 + q] = sp;
+    st += (unsigned long long)P.K * P.chunks;
+    su += (unsigned long long)P.K * P.R;
+    sp += P.K;
+  }
+}
+
+__device__ __forceinline__ int64_t find_segment(const unsigned long long* __restrict__ prefix, int64_t nq,
+                                                unsigned long long x) {
+  int64_t lo = 0, hi = nq;  // last q with prefix[q] <= x
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (prefix[mid] <= x)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+struct WalkArgs {
+  const int4* rec;
+  const int4* node;
+  const QPlan* plans;
+  const unsigned long long* tile_prefix;
+  const Totals* totals;
+  unsigned long long* tile_counter;
+  float* u;
+  uint32_t* visits;
+  int64_t nq;
+  uint32_t n;
+  uint32_t walk_tag, probe_tag;
+};
+
+// One replica: walks from s and t interleaved, a and b summed in FP32 in step
+// order (Eq. hatphi-def), U_p = a - b.  The load of X_{i+1} is issued before
+// the probe entry of X_i is evaluated so the gather latency overlaps the
+// integer work.
+template <bool DEBUG>
+__device__ __forceinline__ float walk_pair(const WalkArgs& A, const Probe& pr, int32_t s, int32_t t, int32_t L,
+                                           uint64_t seed, uint64_t pair) {
+  const int4* __restrict__ rec = A.rec;
+  int4 xs = __ldg(A.node + s), xt = __ldg(A.node + t);
+  uint32_t pis, pit;
+  probe_pi_pair(pr, (uint32_t)xs.x, (uint32_t)xt.x, pis, pit);
+  float a = signed_term(probe_z_from_pi(pr, pis), (uint32_t)xs.w);
+  float b = signed_term(probe_z_from_pi(pr, pit), (uint32_t)xt.w);
+  if (DEBUG) {
+    atomicAdd(A.visits + xs.x, 1u);
+    atomicAdd(A.visits + xt.x, 1u);
+  }
+  if (L == 0) return __fsub_rn(a, b);
+  const uint64_t ws = 2 * pair, wt = ws + 1;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const uint32_t tag = A.walk_tag;
+  Philox4 rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), 0u, tag, k0, k1);
+  Philox4 rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), 0u, tag, k0, k1);
+  int4 ns = __ldg(rec + ((uint32_t)xs.y + __umulhi(rs.y, (uint32_t)xs.z)));
+  int4 nt = __ldg(rec + ((uint32_t)xt.y + __umulhi(rt.y, (uint32_t)xt.z)));
+  for (uint32_t blk = 0;; ++blk) {
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      if (w == 0 && blk == 0) continue;
+      const uint32_t i = blk * 4u + (uint32_t)w;  // ns, nt hold X_i
+      const bool more = i < (uint32_t)L;
+      int4 ns2 = ns, nt2 = nt;
+      if (more) {
+        uint32_t wsw, wtw;
+        if (w == 3) {
+          rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), blk + 1u, tag, k0, k1);
+          rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), blk + 1u, tag, k0, k1);
+          wsw = rs.x;
+          wtw = rt.x;
+        } else {
+          wsw = (w == 0) ? rs.y : (w == 1) ? rs.z : rs.w;
+          wtw = (w == 0) ? rt.y : (w == 1) ? rt.z : rt.w;
+        }
+        ns2 = __ldg(rec + ((uint32_t)ns.y + __umulhi(wsw, (uint32_t)ns.z)));
+        nt2 = __ldg(rec + ((uint32_t)nt.y + __umulhi(wtw, (uint32_t)nt.z)));
+      }
+      probe_pi_pair(pr, (uint32_t)ns.x, (uint32_t)nt.x, pis, pit);
+      a = __fadd_rn(a, signed_term(probe_z_from_pi(pr, pis), (uint32_t)ns.w));
+      b = __fadd_rn(b, signed_term(probe_z_from_pi(pr, pit), (uint32_t)nt.w));
+      if (DEBUG) {
+        atomicAdd(A.visits + ns.x, 1u);
+        atomicAdd(A.visits + nt.x, 1u);
+      }
+      if (!more) return __fsub_rn(a, b);
+      ns = ns2;
+      nt = nt2;
+    }
+  }
+}
+
+// Persistent walk kernel: each warp pops tiles (query, probe k, 32 replicas)
+// from a device counter until the work runs out; lane l runs replica 32c + l.
+template <bool DEBUG>
+__global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkArgs A) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const unsigned long long total = A.totals->tiles;
+  for (;;) {
+    unsigned long long tile = 0;
+    if (lane == 0) tile = atomicAdd(A.tile_counter, 1ull);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= total) return;
+    const int64_t q = find_segment(A.tile_prefix, A.nq, tile);
+    const QPlan& P = A.plans[q];
+    const uint32_t chunks = P.chunks, R = P.R;
+    const unsigned long long local = tile - P.tile_begin;
+    const uint32_t k = (uint32_t)(local / chunks);
+    const uint32_t c = (uint32_t)(local - (unsigned long long)k * chunks);
+    const uint32_t p = c * 32u + lane;
+    if (p >= R) continue;
+    const Probe pr = make_probe(A.n, P.seed, k, A.probe_tag);
+    const uint64_t pair = (uint64_t)k * R + p;
+    const float U = walk_pair<DEBUG>(A, pr, P.s, P.t, P.L, P.seed, pair);
+    A.u[P.u_begin + pair] = U;
+  }
+}
+
+// Q_R per probe (Eq. Q-Ustat): S1, S2 in FP64 over replicas in order.
+__global__ void probe_finish_kernel(const QPlan* __restrict__ plans, int64_t nq,
+                                    const unsigned long long* __restrict__ probe_prefix,
+                                    const Totals* __restrict__ totals, const float* __restrict__ u,
+                                    double* __restrict__ qbuf) {
+  const unsigned long long total = totals->probes;
+  for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < total;
+       j += (unsigned long long)gridDim.x * blockDim.x) {
+    const int64_t q = find_segment(probe_prefix, nq, j);
+    const QPlan& P = plans[q];
+    const unsigned long long k = j - P.probe_begin;
+    const float* x = u + P.u_begin + k * P.R;
+    double S1 = 0.0, S2 = 0.0;
+    for (uint32_t p = 0; p < P.R; ++p) {
+      const double v = (double)x[p];
+      S1 = __dadd_rn(S1, v);
+      S2 = __dadd_rn(S2, __dmul_rn(v, v));
+    }
+    const double Rd = (double)P.R;
+    qbuf[j] = __ddiv_rn(__dsub_rn(__dmul_rn(S1, S1), S2), __dmul_rn(Rd, __dsub_rn(Rd, 1.0)));
+  }
+}
+
+// Median of the G block means of B contiguous probes (Eq. final-estimator).
+__global__ void mom_kernel(const QPlan* __restrict__ plans, const double* __restrict__ qbuf,
+                           double* __restrict__ beta, int32_t* __restrict__ status) {
+  __shared__ double means[4096];
+  const int64_t q = blockIdx.x;
+  const QPlan& P = plans[q];
+  if (P.status != PW_OK || P.K == 0) {
+    if (threadIdx.x == 0) {
+      beta[q] = P.status == PW_OK ? 0.0 : __longlong_as_double(0x7ff8000000000000ll);
+      status[q] = P.status;
+    }
+    return;
+  }
+  for (uint32_t g = threadIdx.x; g < P.G; g += blockDim.x) {
+    const double* x = qbuf + P.probe_begin + (uint64_t)g * P.B;
+    double sum = 0.0;
+    for (uint32_t k = 0; k < P.B; ++k) sum = __dadd_rn(sum, x[k]);
+    means[g] = __ddiv_rn(sum, (double)P.B);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t G = P.G;
+    for (uint32_t i = 1; i < G; ++i) {  // insertion sort
+      const double v = means[i];
+      uint32_t j = i;
+      while (j > 0 && means[j - 1] > v) {
+        means[j] = means[j - 1];
+        --j;
+      }
+      means[j] = v;
+    }
+    const double med = (G & 1u) ? means[G / 2] : __ddiv_rn(__dadd_rn(means[G / 2 - 1], means[G / 2]), 2.0);
+    beta[q] = med;
+    status[q] = PW_OK;
+  }
+}
+
+static int walk_grid(pw_graph* g, bool debug) {
+  static int occ[2] = {0, 0};
+  int& o = occ[debug ? 1 : 0];
+  if (o == 0) {
+    int nb = 0;
+    if (debug)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<true>, kWalkThreads, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<false>, kWalkThreads, 0);
+    o = nb > 0 ? nb : 1;
+  }
+  return g->sm_count * o;
+}
+
+static cudaEvent_t prof_event(pw_graph* g) {
+  ProfileState& P = g->prof;
+  if (!P.pool.empty()) {
+    cudaEvent_t e = P.pool.back();
+    P.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+static void prof_begin(pw_graph* g, cudaStream_t stream, cudaEvent_t* a) {
+  *a = nullptr;
+  if (!g->prof.enabled) return;
+  *a = prof_event(g);
+  cudaEventRecord(*a, stream);
+}
+
+static void prof_end(pw_graph* g, cudaStream_t stream, cudaEvent_t a, int kind) {
+  if (!g->prof.enabled || !a) return;
+  cudaEvent_t b = prof_event(g);
+  cudaEventRecord(b, stream);
+  g->prof.spans.push_back({a, b, kind});
+}
+
+static pw_status launch_walk(pw_graph* g, cudaStream_t stream, bool debug, const WalkArgs& a) {
+  const int grid = walk_grid(g, debug);
+  if (debug)
+    walk_kernel<true><<<grid, kWalkThreads, 0, stream>>>(a);
+  else
+    walk_kernel<false><<<grid, kWalkThreads, 0, stream>>>(a);
+  count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  return PW_OK;
+}
+
+pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t, const double* d_eps,
+                    const int32_t* d_L, const uint64_t* d_seeds, const pw_params* params, double* d_beta,
+                    int32_t* d_status, cudaStream_t stream, DebugOut* dbg) {
+  BudgetArgs ba;
+  pw_status st = resolve_budget(params, g, &ba, nullptr);
+  if (st != PW_OK) return st;
+  if (count < 0) return set_error(PW_ERR_ARG, "count < 0");
+  if (count == 0) return PW_OK;
+  Workspace& ws = g->ws;
+  PW_CUDA_TRY(cudaStreamWaitEvent(stream, ws.last_use, 0));
+  const bool pilot = ba.mode == PW_BUDGET_PILOT;
+  const size_t nq = (size_t)count;
+  if ((st = ensure_buffer(ws.plans, sizeof(QPlan) * nq)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.pilot_plans, sizeof(QPlan) * nq)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.tile_prefix, sizeof(unsigned long long) * 4 * (nq + 1))) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.totals, sizeof(Totals) * 2)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.counters, 64)) != PW_OK) return st;
+  QPlan* plans = (QPlan*)ws.plans.ptr;
+  QPlan* pplans = (QPlan*)ws.pilot_plans.ptr;
+  unsigned long long* prefix = (unsigned long long*)ws.tile_prefix.ptr;
+  unsigned long long* pprefix = prefix + 2 * (nq + 1);
+  Totals* totals = (Totals*)ws.totals.ptr;
+  unsigned long long* counters = (unsigned long long*)ws.counters.ptr;
+  PW_CUDA_TRY(cudaMemsetAsync(counters, 0, 64, stream));
+  const int qthreads = 128;
+  const int qblocks = (int)((count + qthreads - 1) / qthreads);
+  budget_init_kernel<<<qblocks, qthreads, 0, stream>>>(count, d_s, d_t, d_eps, d_L, d_seeds, ba, g->n, g->d_node,
+                                                       plans, pilot ? pplans : nullptr);
+  count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  WalkArgs wa;
+  wa.rec = g->d_rec;
+  wa.node = g->d_node;
+  wa.nq = count;
+  wa.n = (uint32_t)g->n;
+  wa.visits = nullptr;
+  if (pilot) {
+    const size_t pslots = nq * (size_t)ba.K0 * (size_t)ba.R0;
+    if ((st = ensure_buffer(ws.pilot_u, sizeof(float) * pslots)) != PW_OK) return st;
+    scan_kernel<<<1, 1024, 0, stream>>>(pplans, count, pprefix, totals + 1);
+    count_launch();
+    wa.plans = pplans;
+    wa.tile_prefix = pprefix;
+    wa.totals = totals + 1;
+    wa.tile_counter = counters + 1;
+    wa.u = (float*)ws.pilot_u.ptr;
+    wa.walk_tag = kTagWalkPilot;
+    wa.probe_tag = kTagProbePilot;
+    cudaEvent_t ev;
+    prof_begin(g, stream, &ev);
+    if ((st = launch_walk(g, stream, false, wa)) != PW_OK) return st;
+    prof_end(g, stream, ev, 1);
+    if (g->prof.enabled) g->prof.pilot_transitions += 2ull * nq * (uint64_t)ba.K0 * (uint64_t)ba.R0;
+    pilot_budget_kernel<<<qblocks, qthreads, 0, stream>>>(count, plans, pplans, (const float*)ws.pilot_u.ptr, ba,
+                                                          g->d_node);
+    count_launch();
+    PW_CUDA_TRY(cudaGetLastError());
+  }
+  scan_kernel<<<1, 1024, 0, stream>>>(plans, count, prefix, totals);
+  count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  PW_CUDA_TRY(cudaMemcpyAsync(ws.host_totals, totals, sizeof(Totals), cudaMemcpyDeviceToHost, stream));
+  PW_CUDA_TRY(cudaStreamSynchronize(stream));
+  const Totals T = *ws.host_totals;
+  if (dbg && dbg->budget_only) {
+    PW_CUDA_TRY(cudaEventRecord(ws.last_use, stream));
+    return PW_OK;
+  }
+  if ((st = ensure_buffer(ws.u, sizeof(float) * (size_t)T.u_slots)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.q, sizeof(double) * (size_t)T.probes)) != PW_OK) return st;
+  const bool debug = dbg && dbg->visits;
+  wa.plans = plans;
+  wa.tile_prefix = prefix;
+  wa.totals = totals;
+  wa.tile_counter = counters;
+  wa.u = (float*)ws.u.ptr;
+  wa.visits = debug ? dbg->visits : nullptr;
+  wa.walk_tag = kTagWalk;
+  wa.probe_tag = kTagProbe;
+  cudaEvent_t ev_walk;
+  prof_begin(g, stream, &ev_walk);
+  if (T.tiles > 0 && (st = launch_walk(g, stream, debug, wa)) != PW_OK) return st;
+  prof_end(g, stream, ev_walk, 0);
+  if (g->prof.enabled) {
+    g->prof.walk_launches += T.tiles > 0 ? 1 : 0;
+    g->prof.transitions += 2ull * T.steps;
+    g->prof.queries += nq;
+  }
+  cudaEvent_t ev_fin;
+  prof_begin(g, stream, &ev_fin);
+  if (T.probes > 0) {
+    const int fthreads = 128;
+    const unsigned long long want = (T.probes + fthreads - 1) / fthreads;
+    const int fblocks = (int)std::min<unsigned long long>(want, (unsigned long long)g->sm_count * 64);
+    probe_finish_kernel<<<fblocks, fthreads, 0, stream>>>(plans, count, prefix + nq + 1, totals,
+                                                          (const float*)ws.u.ptr, (double*)ws.q.ptr);
+    count_launch();
+    PW_CUDA_TRY(cudaGetLastError());
+  }
+  mom_kernel<<<(unsigned)count, 128, 0, stream>>>(plans, (const double*)ws.q.ptr, d_beta, d_status);
+  count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  prof_end(g, stream, ev_fin, 2);
+  PW_CUDA_TRY(cudaEventRecord(ws.last_use, stream));
+  return PW_OK;
+}
+
+// Host-array batch: stage inputs in pinned memory, run, copy results back.
+static pw_status host_batch(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
+                            const int32_t* L, const uint64_t* seeds, const pw_params* params, double* beta,
+                            int32_t* status, DebugOut* dbg) {
+  if (count < 0) return set_error(PW_ERR_ARG, "count < 0");
+  if (count == 0) return PW_OK;
+  if (!s || !t || !eps || !L || !beta || !status) return set_error(PW_ERR_ARG, "NULL array");
+  Workspace& ws = g->ws;
+  const size_t nq = (size_t)count;
+  const size_t in_bytes = nq * (8 + 8 + 8 + 8 + 4), out_bytes = nq * (8 + 4);
+  pw_status st;
+  if ((st = ensure_host_staging(ws, in_bytes + out_bytes + 64)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.queries, in_bytes + 64)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.results, out_bytes + 64)) != PW_OK) return st;
+  PW_CUDA_TRY(cudaStreamWaitEvent(g->stream, ws.last_use, 0));
+  PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  char* h = (char*)ws.host_staging;
+  memcpy(h, s, nq * 8);
+  memcpy(h + nq * 8, t, nq * 8);
+  memcpy(h + nq * 16, eps, nq * 8);
+  if (seeds) {
+    memcpy(h + nq * 24, seeds, nq * 8);
+  } else {
+    BudgetArgs ba;
+    if ((st = resolve_budget(params, g, &ba, nullptr)) != PW_OK) return st;
+    for (size_t i = 0; i < nq; ++i)
+      ((uint64_t*)(h + nq * 24))[i] = default_seed(ba.global_seed, s[i], t[i], eps[i], L[i]);
+  }
+  memcpy(h + nq * 32, L, nq * 4);
+  char* d = (char*)ws.queries.ptr;
+  PW_CUDA_TRY(cudaMemcpyAsync(d, h, in_bytes, cudaMemcpyHostToDevice, g->stream));
+  double* d_beta = (double*)ws.results.ptr;
+  int32_t* d_status = (int32_t*)((char*)ws.results.ptr + nq * 8);
+  st = run_batch(g, count, (const int64_t*)d, (const int64_t*)(d + nq * 8), (const double*)(d + nq * 16),
+                 (const int32_t*)(d + nq * 32), (const uint64_t*)(d + nq * 24), params, d_beta, d_status, g->stream,
+                 dbg);
+  if (st != PW_OK) return st;
+  if (dbg && dbg->budget_only) return PW_OK;
+  char* ho = h + in_bytes;
+  PW_CUDA_TRY(cudaMemcpyAsync(ho, ws.results.ptr, out_bytes, cudaMemcpyDeviceToHost, g->stream));
+  PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  memcpy(beta, ho, nq * 8);
+  memcpy(status, ho + nq * 8, nq * 4);
+  return PW_OK;
+}
+
+static pw_status copy_plan(pw_graph* g, int64_t q, QPlan* out) {
+  PW_CUDA_TRY(cudaMemcpyAsync(out, (QPlan*)g->ws.plans.ptr + q, sizeof(QPlan), cudaMemcpyDeviceToHost, g->stream));
+  PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return PW_OK;
+}
+
+}  // namespace pw
+
+using namespace pw;
+
+extern "C" {
+
+pw_status pw_query_batch(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
+                         const int32_t* L, const uint64_t* seeds, const pw_params* params, double* beta_hat,
+                         int32_t* per_query_status) {
+  if (!g) return set_error(PW_ERR_ARG, "graph is NULL");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  return host_batch(g, count, s, t, eps, L, seeds, params, beta_hat, per_query_status, nullptr);
+}
+
+pw_status pw_query_batch_device(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t,
+                                const double* d_eps, const int32_t* d_L, const uint64_t* d_seeds,
+                                const pw_params* params, double* d_beta_hat, int32_t* d_status, void* stream) {
+  if (!g) return set_error(PW_ERR_ARG, "graph is NULL");
+  if (count > 0 && (!d_s || !d_t || !d_eps || !d_L || !d_beta_hat || !d_status))
+    return set_error(PW_ERR_ARG, "NULL device array");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  return run_batch(g, count, d_s, d_t, d_eps, d_L, d_seeds, params, d_beta_hat, d_status, (cudaStream_t)stream,
+                   nullptr);
+}
+
+pw_status pw_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
+                   const pw_params* params, double* beta_hat) {
+  if (!g || !beta_hat) return set_error(PW_ERR_ARG, "NULL argument");
+  if (s < 0 || s >= g->n || t < 0 || t >= g->n) return set_error(PW_ERR_ARG, "node id out of range");
+  if (!(eps > 0.0 && eps < 1.0)) return set_error(PW_ERR_ARG, "eps must lie in (0, 1)");
+  if (L < 0) return set_error(PW_ERR_ARG, "L < 0");
+  if (s == t) {
+    *beta_hat = 0.0;
+    return PW_OK;
+  }
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  BudgetArgs ba;
+  pw_status st = resolve_budget(params, g, &ba, nullptr);
+  if (st != PW_OK) return st;
+  const uint64_t sd = seed ? *seed : default_seed(ba.global_seed, s, t, eps, L);
+  int32_t qst = 0;
+  st = host_batch(g, 1, &s, &t, &eps, &L, &sd, params, beta_hat, &qst, nullptr);
+  if (st != PW_OK) return st;
+  if (qst != PW_OK) return set_error((pw_status)qst, "query rejected (budget beyond 2^32 probes or replicas)");
+  return PW_OK;
+}
+
+pw_status pw_budget(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
+                    const pw_params* params, uint64_t* B, uint64_t* G, uint64_t* K, uint64_t* R) {
+  if (!g) return set_error(PW_ERR_ARG, "graph is NULL");
+  if (s < 0 || s >= g->n || t < 0 || t >= g->n) return set_error(PW_ERR_ARG, "node id out of range");
+  if (!(eps > 0.0 && eps < 1.0)) return set_error(PW_ERR_ARG, "eps must lie in (0, 1)");
+  if (L < 0) return set_error(PW_ERR_ARG, "L < 0");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  BudgetArgs ba;
+  pw_status st = resolve_budget(params, g, &ba, nullptr);
+  if (st != PW_OK) return st;
+  const uint64_t sd = seed ? *seed : default_seed(ba.global_seed, s, t, eps, L);
+  DebugOut dbg;
+  dbg.budget_only = true;
+  double beta;
+  int32_t qst;
+  st = host_batch(g, 1, &s, &t, &eps, &L, &sd, params, &beta, &qst, &dbg);
+  if (st != PW_OK) return st;
+  QPlan P;
+  if ((st = copy_plan(g, 0, &P)) != PW_OK) return st;
+  if (P.status != PW_OK) return set_error((pw_status)P.status, "query rejected");
+  if (B) *B = P.B;
+  if (G) *G = P.G;
+  if (K) *K = P.K;
+  if (R) *R = P.R;
+  return PW_OK;
+}
+
+pw_status pw_debug_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
+                         const pw_params* params, double* beta_hat, uint64_t* budget, double* pilot, double* q,
+                         int64_t q_cap, float* u, int64_t u_cap, uint32_t* visits) {
+  if (!g || !beta_hat) return set_error(PW_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  BudgetArgs ba;
+  pw_status st = resolve_budget(params, g, &ba, nullptr);
+  if (st != PW_OK) return st;
+  const uint64_t sd = seed ? *seed : default_seed(ba.global_seed, s, t, eps, L);
+  DebugOut dbg;
+  DeviceBuffer vis;
+  if (visits) {
+    if ((st = ensure_buffer(vis, sizeof(uint32_t) * (size_t)g->n)) != PW_OK) return st;
+    PW_CUDA_TRY(cudaMemsetAsync(vis.ptr, 0, sizeof(uint32_t) * (size_t)g->n, g->stream));
+    dbg.visits = (uint32_t*)vis.ptr;
+  }
+  int32_t qst = 0;
+  st = host_batch(g, 1, &s, &t, &eps, &L, &sd, params, beta_hat, &qst, &dbg);
+  if (st == PW_OK && qst != PW_OK) st = set_error((pw_status)qst, "query rejected");
+  QPlan P;
+  memset(&P, 0, sizeof P);
+  if (st == PW_OK) st = copy_plan(g, 0, &P);
+  if (st == PW_OK) {
+    if (budget) {
+      budget[0] = P.B;
+      budget[1] = P.G;
+      budget[2] = P.K;
+      budget[3] = P.R;
+    }
+    if (pilot) {
+      pilot[0] = P.sigma2;
+      pilot[1] = P.qbar;
+      pilot[2] = P.theta;
+    }
+    const uint64_t K = P.K, KR = (uint64_t)P.K * P.R;
+    if ((q && (uint64_t)q_cap < K) || (u && (uint64_t)u_cap < KR)) {
+      st = set_error(PW_ERR_ARG, "q_cap or u_cap too small");
+    } else {
+      if (q && K) cudaMemcpyAsync(q, (double*)g->ws.q.ptr + P.probe_begin, sizeof(double) * K, cudaMemcpyDeviceToHost,
+                                  g->stream);
+      if (u && KR) cudaMemcpyAsync(u, (float*)g->ws.u.ptr + P.u_begin, sizeof(float) * KR, cudaMemcpyDeviceToHost,
+                                   g->stream);
+      if (visits)
+        cudaMemcpyAsync(visits, vis.ptr, sizeof(uint32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, g->stream);
+      cudaError_t e = cudaStreamSynchronize(g->stream);
+      if (e != cudaSuccess) st = cuda_error(e, "debug copy-out");
+    }
+  }
+  free_buffer(vis);
+  return st;
+}
+
+pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stats* out) {
+  if (!g) return set_error(PW_ERR_ARG, "graph is NULL");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  ProfileState& P = g->prof;
+  for (auto& sp : P.spans) {
+    PW_CUDA_TRY(cudaEventSynchronize(sp.b));
+    float ms = 0.f;
+    PW_CUDA_TRY(cudaEventElapsedTime(&ms, sp.a, sp.b));
+    (sp.kind == 0 ? P.walk_ms : sp.kind == 1 ? P.pilot_ms : P.finish_ms) += ms;
+    P.pool.push_back(sp.a);
+    P.pool.push_back(sp.b);
+  }
+  P.spans.clear();
+  if (out) {
+    out->walk_ms = P.walk_ms;
+    out->pilot_ms = P.pilot_ms;
+    out->finish_ms = P.finish_ms;
+    out->walk_launches = P.walk_launches;
+    out->transitions = P.transitions;
+    out->pilot_transitions = P.pilot_transitions;
+    out->queries = P.queries;
+  }
+  if (reset) {
+    P.walk_ms = P.pilot_ms = P.finish_ms = 0;
+    P.walk_launches = P.transitions = P.pilot_transitions = P.queries = 0;
+  }
+  P.enabled = enable != 0;
+  return PW_OK;
+}
+
+pw_status pw_debug_batch_probe_q(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t,
+                                 const double* eps, const int32_t* L, const uint64_t* seeds,
+                                 const pw_params* params, double* beta_hat, int32_t* per_query_status,
+                                 uint64_t* KR, int64_t n_sel, const int64_t* sel_query, const int64_t* sel_probe,
+                                 double* q_sel) {
+  if (!g) return set_error(PW_ERR_ARG, "graph is NULL");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  pw_status st = host_batch(g, count, s, t, eps, L, seeds, params, beta_hat, per_query_status, nullptr);
+  if (st != PW_OK || count == 0) return st;
+  std::vector<QPlan> plans((size_t)count);
+  PW_CUDA_TRY(cudaMemcpyAsync(plans.data(), g->ws.plans.ptr, sizeof(QPlan) * (size_t)count, cudaMemcpyDeviceToHost,
+                              g->stream));
+  PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (KR)
+    for (int64_t i = 0; i < count; ++i) {
+      KR[2 * i] = plans[(size_t)i].K;
+      KR[2 * i + 1] = plans[(size_t)i].R;
+    }
+  for (int64_t i = 0; i < n_sel; ++i) {
+    const int64_t qi = sel_query[i], k = sel_probe[i];
+    if (qi < 0 || qi >= count || k < 0 || (uint64_t)k >= plans[(size_t)qi].K)
+      return set_error(PW_ERR_ARG, "selection out of range");
+    PW_CUDA_TRY(cudaMemcpyAsync(q_sel + i, (double*)g->ws.q.ptr + plans[(size_t)qi].probe_begin + k, sizeof(double),
+                                cudaMemcpyDeviceToHost, g->stream));
+  }
+  PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return PW_OK;
+}
+
+}  // extern "C"

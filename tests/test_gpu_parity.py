@@ -1,0 +1,288 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle.
+
+Integer work is compared bit for bit (Philox words, probe vectors, walk
+trajectories, visit counts).  Floating point: U_p (FP32, fixed step order)
+is bit-exact; Q_R and beta_hat use FP64 sums in the oracle's order, so they
+are bit-exact too; every comparison also states the benchmark spec's tolerance of
+1e-5 relative, which is the bar."""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+from pw_inputs import (barabasi_albert, complete_graph, cycle_graph, er_cycle, eps_uniform, path_graph,
+                       query_seeds, uniform_pairs)
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-5
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def pw():
+    from paper_2512_05460_gb300 import build
+
+    build.build()
+    from paper_2512_05460_gb300 import probewalk
+
+    probewalk.lib()
+    return probewalk
+
+
+@pytest.fixture(scope="module")
+def tiny(pw, tiny_graph):
+    g = pw.Graph(tiny_graph.row_ptr, tiny_graph.col_idx)
+    yield tiny_graph, g
+    g.close()
+
+
+@pytest.fixture(scope="module")
+def ba_graph():
+    return barabasi_albert(100_000, 5, 1)
+
+
+@pytest.fixture(scope="module")
+def ba(pw, ba_graph):
+    g = pw.Graph(ba_graph.row_ptr, ba_graph.col_idx)
+    yield ba_graph, g
+    g.close()
+
+
+def test_graph_info(pw, tiny):
+    host, g = tiny
+    info = pw.pw_graph_info(g.handle)
+    assert info["n"] == host.n and info["nnz"] == host.nnz
+    assert info["d_min"] == host.d_min and info["d_max"] == host.d_max
+    assert info["bipartite"] == host.is_bipartite()
+
+
+def test_philox_known_answers_on_device(pw, tiny):
+    _, g = tiny
+    with open(os.path.join(GOLDEN, "philox_kat.txt")) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    for row in rows:
+        v = [int(x, 16) for x in row]
+        assert [int(x) for x in pw.pw_debug_philox(g.handle, v[0:4], v[4:6])] == v[6:10]
+
+
+@pytest.mark.parametrize("graph_fn", [lambda: er_cycle(200, 8 / 199, 0), lambda: complete_graph(7),
+                                      lambda: cycle_graph(16), lambda: barabasi_albert(3000, 3, 5)])
+def test_probe_vectors_bit_exact(pw, oracle_lib, graph_fn):
+    host = graph_fn()
+    with pw.Graph(host.row_ptr, host.col_idx) as g:
+        for seed in (1, 2**64 - 3, 987654321):
+            for k in (0, 1, 77, 2**31 + 5):
+                for tag in (pw.TAG_PROBE, pw.TAG_PROBE_PILOT):
+                    z_dev, r_dev = pw.pw_debug_probe(g.handle, host.n, seed, k, tag)
+                    z_orc, _, r_orc = oracle.probe_vector(host.n, seed, k, tag)
+                    assert r_dev == r_orc
+                    np.testing.assert_array_equal(z_dev, z_orc)
+
+
+def test_trajectories_bit_exact(pw, oracle_lib, tiny):
+    host, g = tiny
+    rng = np.random.default_rng(0)
+    for _ in range(40):
+        start = int(rng.integers(host.n))
+        L = int(rng.integers(0, 70))
+        seed = int(rng.integers(0, 2**63))
+        wid = int(rng.integers(0, 2**40))
+        tag = int(rng.choice([pw.TAG_WALK, pw.TAG_WALK_PILOT]))
+        np.testing.assert_array_equal(pw.pw_debug_walk(g.handle, start, L, seed, wid, tag),
+                                      oracle.walk(host, start, L, seed, wid, tag))
+
+
+def _compare_query(pw, host, g, s, t, eps, L, seed, params, cfg):
+    dev = pw.pw_debug_query(g.handle, host.n, s, t, eps, L, seed, params, q_cap=1 << 22, u_cap=1 << 26,
+                            want_visits=True)
+    orc = oracle.query(host, s, t, eps, L, seed, cfg, want_q=True, want_u=True, want_visits=True)
+    assert (dev["B"], dev["G"], dev["K"], dev["R"]) == (orc["B"], orc["G"], orc["K"], orc["R"])
+    assert dev["sigma2_hat"] == orc["sigma2_hat"] and dev["q_bar"] == orc["q_bar"]
+    np.testing.assert_array_equal(dev["u"], orc["u"])          # every U_p, bit for bit
+    np.testing.assert_array_equal(dev["visits"], orc["visits"])  # visit counts
+    np.testing.assert_array_equal(dev["q"], orc["q"])
+    assert dev["beta"] == orc["beta"]
+    assert abs(dev["beta"] - orc["beta"]) <= REL_TOL * abs(orc["beta"])
+    return dev, orc
+
+
+def test_debug_query_pilot_bit_exact(pw, oracle_lib, tiny):
+    host, g = tiny
+    for s, t, seed in ((3, 77, 12345), (0, 199, 1), (150, 9, 2**62 + 11)):
+        _compare_query(pw, host, g, s, t, 0.2, 32, seed, None, oracle.budget_cfg())
+
+
+@pytest.mark.parametrize("B,G,R,L", [(3, 1, 2, 0), (5, 3, 7, 1), (4, 5, 45, 13), (2, 3, 70, 33), (1, 1, 33, 4)])
+def test_debug_query_fixed_ragged_bit_exact(pw, oracle_lib, tiny, B, G, R, L):
+    host, g = tiny
+    params = pw.make_params(budget_mode=pw.PW_BUDGET_FIXED, B=B, G=G, R=R)
+    cfg = oracle.budget_cfg(mode=oracle.MODE_FIXED, B=B, G=G, R=R)
+    _compare_query(pw, host, g, 10, 20, 0.3, L, 424242, params, cfg)
+
+
+@pytest.mark.parametrize("mode", ["THEORY", "SCALED"])
+def test_budget_modes_match_oracle(pw, oracle_lib, tiny, mode):
+    host, g = tiny
+    if mode == "THEORY":
+        params = pw.make_params(budget_mode=pw.PW_BUDGET_THEORY)
+        cfg = oracle.budget_cfg(mode=oracle.MODE_THEORY)
+    else:
+        params = pw.make_params(budget_mode=pw.PW_BUDGET_SCALED, c_B=0.001, c_R=0.01, R_max=500)
+        cfg = oracle.budget_cfg(mode=oracle.MODE_SCALED, c_B=0.001, c_R=0.01, R_max=500)
+    for s, t, eps, L in ((1, 2, 0.5, 4), (5, 100, 0.1, 32), (7, 8, 0.05, 0)):
+        dev = pw.pw_budget(g.handle, s, t, eps, L, 99, params)
+        orc = oracle.budget(host, s, t, eps, L, 99, cfg)
+        assert (dev["B"], dev["G"], dev["K"], dev["R"]) == (orc["B"], orc["G"], orc["K"], orc["R"])
+
+
+def test_tiny_batch_parity_and_accuracy(pw, oracle_lib, tiny):
+    """64 queries of the tiny workload: per-query beta_hat equal to the oracle
+    (tolerance 1e-5 rel; in fact bit-exact) and >= 95% within eps of the exact beta."""
+    host, g = tiny
+    s, t = uniform_pairs(host.n, 64, 100)
+    seeds = query_seeds(64, 200)
+    beta, st = pw.pw_query_batch(g.handle, s, t, 0.2, 32, seeds)
+    assert np.all(st == 0)
+    ob, _, ost = oracle.query_many(host, s, t, 0.2, 32, seeds)
+    assert np.all(ost == 0)
+    np.testing.assert_allclose(beta, ob, rtol=REL_TOL, atol=0)
+    assert np.array_equal(beta, ob)
+    ex = exact.exact_beta_matrix(host.row_ptr, host.col_idx, host.n)[s, t]
+    assert (np.abs(beta - ex) / ex <= 0.2).mean() >= 0.95
+
+
+def test_alone_equals_in_mix(pw, tiny):
+    host, g = tiny
+    s, t = uniform_pairs(host.n, 24, 5)
+    eps = eps_uniform(24, 0.15, 0.4, 6)
+    L = np.random.default_rng(7).integers(0, 40, size=24).astype(np.int32)
+    seeds = query_seeds(24, 8)
+    mix, st = pw.pw_query_batch(g.handle, s, t, eps, L, seeds)
+    assert np.all(st == 0)
+    for i in range(24):
+        alone = pw.pw_query(g.handle, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i]))
+        assert alone == mix[i]
+    # reversed order inside the batch
+    rev, _ = pw.pw_query_batch(g.handle, s[::-1], t[::-1], eps[::-1], L[::-1], seeds[::-1])
+    np.testing.assert_array_equal(rev[::-1], mix)
+
+
+def test_edge_cases(pw, oracle_lib, tiny):
+    host, g = tiny
+    # empty batch
+    b, st = pw.pw_query_batch(g.handle, np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0))
+    assert b.size == 0
+    # s == t gives exactly 0 without walks; invalid queries get a per-query status
+    s = np.array([5, 5, -1, 3, 3, 4])
+    t = np.array([5, 6, 2, 200, 7, 9])
+    eps = np.array([0.2, 0.2, 0.2, 0.2, 1.5, 0.2])
+    L = np.array([32, 32, 32, 32, 32, -3])
+    beta, st = pw.pw_query_batch(g.handle, s, t, eps, L, query_seeds(6, 1))
+    assert beta[0] == 0.0 and st[0] == 0
+    assert st[1] == 0 and np.isfinite(beta[1])
+    assert list(st[2:]) == [pw.PW_ERR_ARG] * 4
+    assert np.all(np.isnan(beta[2:]))
+    assert pw.pw_query(g.handle, 9, 9, 0.2, 32) == 0.0
+    for bad in ((0, 200, 0.2, 32), (0, 1, 0.0, 32), (0, 1, 1.0, 32), (0, 1, 0.2, -1)):
+        with pytest.raises(pw.PWError):
+            pw.pw_query(g.handle, *bad)
+    # default seeds: library and oracle agree on the seed, hence on the estimate
+    params = pw.make_params(seed=777, budget_mode=pw.PW_BUDGET_FIXED, B=2, G=1, R=5)
+    got = pw.pw_query(g.handle, 1, 2, 0.3, 6, None, params)
+    want = oracle.query(host, 1, 2, 0.3, 6, oracle.default_seed(777, 1, 2, 0.3, 6),
+                        oracle.budget_cfg(mode=oracle.MODE_FIXED, B=2, G=1, R=5))["beta"]
+    assert got == want
+
+
+def test_invalid_graphs_rejected(pw):
+    rp = np.array([0, 1, 2, 3])
+    with pytest.raises(pw.PWError):  # asymmetric
+        pw.pw_graph_load(rp, np.array([1, 2, 0]))
+    with pytest.raises(pw.PWError):  # disconnected: two edges 0-1, 2-3
+        pw.pw_graph_load(np.array([0, 1, 2, 3, 4]), np.array([1, 0, 3, 2]))
+    with pytest.raises(pw.PWError):  # isolated node 2
+        pw.pw_graph_load(np.array([0, 1, 2, 2]), np.array([1, 0]))
+    with pytest.raises(pw.PWError):  # self-loop
+        pw.pw_graph_load(np.array([0, 2, 3]), np.array([0, 1, 0]))
+
+
+def test_bipartite_flag(pw):
+    p = path_graph(6)
+    with pw.Graph(p.row_ptr, p.col_idx) as g:
+        assert g.info["bipartite"]
+
+
+def test_device_api_matches_host_api(pw, tiny):
+    torch = pytest.importorskip("torch")
+    host, g = tiny
+    s, t = uniform_pairs(host.n, 40, 11)
+    seeds = query_seeds(40, 12)
+    eps = np.full(40, 0.25)
+    L = np.full(40, 20, np.int32)
+    want, _ = pw.pw_query_batch(g.handle, s, t, eps, L, seeds)
+    dev = torch.device("cuda:0")
+    ds, dt = torch.from_numpy(s).to(dev), torch.from_numpy(t).to(dev)
+    de, dl = torch.from_numpy(eps).to(dev), torch.from_numpy(L).to(dev)
+    dseed = torch.from_numpy(seeds.view(np.int64)).to(dev)
+    beta = torch.empty(40, dtype=torch.float64, device=dev)
+    status = torch.empty(40, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        pw.pw_query_batch_device(g.handle, 40, ds, dt, de, dl, dseed, beta, status, stream=stream)
+    stream.synchronize()
+    np.testing.assert_array_equal(beta.cpu().numpy(), want)
+    assert int(status.abs().sum()) == 0
+
+
+# ---------------------------------------------------------------------------
+# Full-size BA workload (n = 100,000, m = 5; 1,000 queries; L = 200; eps = 0.1)
+# in the bench's launch configuration.  The oracle recomputes sampled probes
+# one by one, and two whole queries.
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def ba_batch(pw, ba):
+    host, g = ba
+    s, t = uniform_pairs(host.n, 1000, 101)
+    seeds = query_seeds(1000, 1001)
+    rng = np.random.default_rng(3)
+    sel_q = rng.integers(0, 1000, size=24)
+    # probe indices are drawn below K for every query (K = 3700 at eps = 0.1)
+    sel_k = rng.integers(0, 3700, size=24)
+    beta, st, KR, qsel = pw.pw_debug_batch_probe_q(g.handle, s, t, 0.1, 200, seeds, sel_q, sel_k)
+    return dict(host=host, s=s, t=t, seeds=seeds, beta=beta, st=st, KR=KR, sel_q=sel_q, sel_k=sel_k, qsel=qsel)
+
+
+def test_ba_full_size_sampled_probes(oracle_lib, ba_batch):
+    b = ba_batch
+    assert np.all(b["st"] == 0)
+    assert np.all(b["KR"][:, 0] == 3700)
+    for i, (qi, k) in enumerate(zip(b["sel_q"], b["sel_k"])):
+        R = int(b["KR"][qi, 1])
+        budget = oracle.budget(b["host"], int(b["s"][qi]), int(b["t"][qi]), 0.1, 200, int(b["seeds"][qi]))
+        assert budget["R"] == R and budget["K"] == 3700
+        want = oracle.probe_q(b["host"], int(b["s"][qi]), int(b["t"][qi]), 200, int(b["seeds"][qi]), R, [k])[0]
+        assert b["qsel"][i] == want
+        assert abs(b["qsel"][i] - want) <= REL_TOL * abs(want) + 1e-300
+
+
+def test_ba_full_size_whole_queries(oracle_lib, ba_batch):
+    b = ba_batch
+    for qi in (0, 517):
+        want = oracle.query(b["host"], int(b["s"][qi]), int(b["t"][qi]), 0.1, 200, int(b["seeds"][qi]))
+        assert b["beta"][qi] == want["beta"]
+
+
+def test_ba_full_size_accuracy_vs_series(ba_batch):
+    """>= 95% of sampled queries within eps of beta^(L) (series oracle)."""
+    b = ba_batch
+    host = b["host"]
+    idx = np.arange(0, 1000, 1000 // 64)[:64]
+    want = exact.series_beta_many(host.row_ptr, host.col_idx, host.n, b["s"][idx], b["t"][idx], 200)
+    rel = np.abs(b["beta"][idx] - want) / want
+    assert (rel <= 0.1).mean() >= 0.95
