@@ -148,44 +148,54 @@ def workload_inputs(wl: dict, rank: int):
     return host, s, t, seeds
 
 
-def cpu_oracle_sample(host, s, t, seeds, wl, count: int):
+def cpu_oracle_sample(host, s, t, seeds, wl, n_queries: int, probes_per_query: int, offset: int = 0):
+    """The oracle, as it stands, on a bounded sample of the workload: for each
+    of `n_queries` queries (one host thread each) its budget (pilot included)
+    and its first `probes_per_query` probes.  Returns queries/s = (sum over the
+    sampled queries of the fraction of their transitions done) / wall time."""
+    import concurrent.futures as cf
+
     import oracle
 
     oracle.build()
-    threads = oracle.max_threads()
-    count = min(count, s.size)
+    idx = [(offset + i) % s.size for i in range(n_queries)]
+
+    def one(i):
+        b = oracle.budget(host, int(s[i]), int(t[i]), wl["eps"], wl["L"], int(seeds[i]))
+        P = min(probes_per_query, b["K"])
+        oracle.probe_q(host, int(s[i]), int(t[i]), wl["L"], int(seeds[i]), b["R"], np.arange(P))
+        pilot = 2 * 64 * 32 * wl["L"]
+        done = pilot + 2 * P * b["R"] * wl["L"]
+        total = pilot + 2 * b["K"] * b["R"] * wl["L"]
+        return done / total, done
+
     t0 = time.perf_counter()
-    beta, _, st = oracle.query_many(host, s[:count], t[:count], wl["eps"], wl["L"], seeds[:count], threads=threads)
+    with cf.ThreadPoolExecutor(max_workers=n_queries) as ex:
+        res = list(ex.map(one, idx))
     dt = time.perf_counter() - t0
-    assert np.all(st == 0)
-    return count / dt, dt, threads, count
+    frac = sum(r[0] for r in res)
+    steps = sum(r[1] for r in res)
+    return frac / dt, dt, n_queries, steps / dt
 
 
 def run_reference(args, wl, world, rank):
-    """CPU oracle arm: each step runs one query per host core, in parallel."""
+    """CPU oracle arm: each step is a bounded sample (budget plus the first
+    probes of one query per host core), scaled to queries/s."""
     if rank != 0:
         return
     host, s, t, seeds = workload_inputs(wl, 0)
-    import oracle
-
-    oracle.build()
-    threads = oracle.max_threads()
-    per_step = min(threads, s.size) if wl["queries"] > 64 else s.size
-    times = []
+    threads = args.cpu_threads or os.cpu_count()
+    vals, times = [], []
     for i in range(args.warmup + args.steps):
-        lo = (i * per_step) % s.size
-        idx = np.arange(lo, lo + per_step) % s.size
-        t0 = time.perf_counter()
-        _, _, st = oracle.query_many(host, s[idx], t[idx], wl["eps"], wl["L"], seeds[idx], threads=threads)
-        dt = time.perf_counter() - t0
-        assert np.all(st == 0)
+        qps, dt, nq, sps = cpu_oracle_sample(host, s, t, seeds, wl, threads, args.cpu_probes, offset=i * threads)
         if i >= args.warmup:
+            vals.append(qps)
             times.append(dt)
-    total = sum(times)
-    value = per_step * len(times) / total
-    sample = f"{per_step} queries of the {wl['queries']}-query batch per step, one OpenMP thread per query"
+    value = sum(vals) / len(vals)
+    sample = (f"per step: budget (pilot included) and the first {args.cpu_probes} probes of each of {threads} queries, "
+              f"one host thread per query; queries/s = completed fraction of the sampled queries / wall time")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {wl['desc']}; {wl['queries']} uniform pairs; L={wl['L']}; "
                                    f"eps={wl['eps']}; delta=0.01; PILOT budget", "l2": "n/a (CPU)"},
@@ -205,11 +215,13 @@ def run_ours(args, wl, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     host, s, t, seeds = workload_inputs(wl, rank)
+    if args.queries:
+        s, t, seeds = s[:args.queries], t[:args.queries], seeds[:args.queries]
     nq = s.size
     eps = np.full(nq, wl["eps"])
     L = np.full(nq, wl["L"], np.int32)
     g = pw.Graph(host.row_ptr, host.col_idx, device=local)
-    params = pw.make_params(c_B=args.c_B) if args.c_B else None
+    params = pw.make_params(c_B=args.c_B, walk_mode=args.walk_mode)
     d_s = torch.from_numpy(s).to(dev)
     d_t = torch.from_numpy(t).to(dev)
     d_eps = torch.from_numpy(eps).to(dev)
@@ -252,6 +264,7 @@ def run_ours(args, wl, world, rank, local):
     clocks = sampler.stop()
     launches = pw.pw_launch_count(reset=True)
     prof = pw.pw_profile(g.handle, enable=False, reset=True)
+    walk_mode = prof.get("walk_mode", 0)
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = max_over_ranks(world, sum(step_ms), dev)
     beta = d_beta.cpu().numpy()
@@ -262,19 +275,19 @@ def run_ours(args, wl, world, rank, local):
     walk_steps_per_s = world * (prof["transitions"] + prof["pilot_transitions"]) / (total_ms / 1000.0)
 
     # ---- end to end through the host-array entry point -----------------------
-    for _ in range(1):
-        pw.pw_query_batch(g.handle, s, t, eps, L, seeds, params)
     e2e_times = []
-    for i in range(args.steps):
+    for i in range(args.steps if not args.no_e2e else 0):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b2, st2 = pw.pw_query_batch(g.handle, s, t, eps, L, seeds, params)
         e2e_times.append(time.perf_counter() - t0)
         assert np.all(st2 == 0)
-    assert np.array_equal(b2, beta), "host and device entry points disagree"
-    e2e_total = max_over_ranks(world, sum(e2e_times), dev)
-    e2e_value = world * nq * args.steps / e2e_total
+        assert np.array_equal(b2, beta), "host and device entry points disagree"
+    e2e_value = None
+    if e2e_times:
+        e2e_total = max_over_ranks(world, sum(e2e_times), dev)
+        e2e_value = world * nq * len(e2e_times) / e2e_total
 
     # ---- one query per launch (the plain form), on a prefix of the batch ------
     plain_n = min(args.plain, nq)
@@ -297,9 +310,12 @@ def run_ours(args, wl, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        qps, dt, threads, cnt = cpu_oracle_sample(host, s, t, seeds, wl, args.cpu_queries or os.cpu_count())
+        threads = args.cpu_threads or os.cpu_count()
+        qps, dt, cnt, sps = cpu_oracle_sample(host, s, t, seeds, wl, threads, args.cpu_probes)
         cpu = {"value": qps, "unit": "queries/s", "cores": threads, "kind": "oracle",
-               "sample": f"first {cnt} queries of the batch, one OpenMP thread per query, {dt:.1f} s"}
+               "sample": f"budget (pilot included) and the first {args.cpu_probes} probes of each of the first {cnt} "
+                         f"queries, one host thread per query, {dt:.1f} s; queries/s = completed fraction / wall",
+               "walk_steps_per_s": sps}
 
     if rank == 0:
         lat_ms = sorted(1000 * x for x in lat)
@@ -317,6 +333,7 @@ def run_ours(args, wl, world, rank, local):
                        "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                        "parallelism": f"query sharding x{world}"},
             "walk_steps_per_s": walk_steps_per_s,
+            "walk_kernel": {1: "per-visit probe evaluation", 2: "per-probe shared-memory table"}.get(walk_mode, "?"),
             "transitions_per_step": transitions_per_step,
             "plain_queries_per_s": plain_qps, "plain_sample": plain_n,
             "batched_over_plain": (value / world) / plain_qps if plain_qps else None,
@@ -342,8 +359,12 @@ def main():
     ap.add_argument("--workload", default="ba-1e5", choices=sorted(WORKLOADS))
     ap.add_argument("--plain", type=int, default=64, help="queries timed in the one-query-per-launch form")
     ap.add_argument("--c_B", type=float, default=0.0)
-    ap.add_argument("--cpu-queries", type=int, default=0)
+    ap.add_argument("--queries", type=int, default=0, help="use only the first N queries (small profiling runs)")
+    ap.add_argument("--walk-mode", type=int, default=0, help="0 autotuned, 1 per-visit, 2 probe table")
+    ap.add_argument("--cpu-threads", type=int, default=0)
+    ap.add_argument("--cpu-probes", type=int, default=40, help="probes per sampled query in the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -71,8 +71,8 @@ typedef struct pw_params {
   uint64_t B, G, R;        /* FIXED mode values (B >= 1, G >= 1, R >= 2) */
   uint64_t R_max;          /* PILOT / SCALED clamp; 0 -> 4096 */
   uint64_t seed;           /* global seed for queries that pass no seed */
-  int32_t tiles_per_claim; /* walk-kernel tiles claimed per work-queue pop; 0 -> autotuned */
-  int32_t block_threads;   /* walk-kernel block size; 0 -> autotuned */
+  int32_t walk_mode;       /* 0 autotuned; 1 probe entries evaluated per visit; 2 per-probe shared-memory table */
+  int32_t reserved1;
 } pw_params;
 
 typedef struct pw_graph pw_graph;
@@ -194,6 +194,8 @@ typedef struct pw_profile_stats {
   uint64_t transitions;
   uint64_t pilot_transitions;
   uint64_t queries;
+  int32_t walk_mode;           /* walk kernel of the last batch: 1 per-visit probe evaluation, 2 probe table */
+  int32_t reserved;
 } pw_profile_stats;
 pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stats* out);
 

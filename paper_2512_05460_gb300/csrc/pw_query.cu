@@ -229,29 +229,52 @@ struct WalkArgs {
   uint32_t walk_tag, probe_tag;
 };
 
+// Probe entries evaluated on the fly (Section 3.3 generator): one cycle-walk
+// queue for the two walks so a lane pays iter(s) + iter(t) Feistel passes.
+struct ZOnTheFly {
+  const Probe& pr;
+  __device__ __forceinline__ void pair(uint32_t vs, uint32_t vt, int& zs, int& zt) const {
+    uint32_t pis, pit;
+    probe_pi_pair(pr, vs, vt, pis, pit);
+    zs = probe_z_from_pi(pr, pis);
+    zt = probe_z_from_pi(pr, pit);
+  }
+};
+
+// Probe entries read from the block's 2-bit table of z^(k) (built once per probe).
+struct ZTable {
+  const uint32_t* tab;
+  __device__ __forceinline__ static int decode(uint32_t c) { return c == 0 ? 0 : (c == 1 ? 1 : -1); }
+  __device__ __forceinline__ void pair(uint32_t vs, uint32_t vt, int& zs, int& zt) const {
+    zs = decode((tab[vs >> 4] >> ((vs & 15u) << 1)) & 3u);
+    zt = decode((tab[vt >> 4] >> ((vt & 15u) << 1)) & 3u);
+  }
+};
+
+__device__ __forceinline__ uint32_t z_code(int z) { return z == 0 ? 0u : (z > 0 ? 1u : 3u); }
+
 // One replica: walks from s and t interleaved, a and b summed in FP32 in step
 // order (Eq. hatphi-def), U_p = a - b.  The load of X_{i+1} is issued before
 // the probe entry of X_i is evaluated so the gather latency overlaps the
 // integer work.
-template <bool DEBUG>
-__device__ __forceinline__ float walk_pair(const WalkArgs& A, const Probe& pr, int32_t s, int32_t t, int32_t L,
-                                           uint64_t seed, uint64_t pair) {
-  const int4* __restrict__ rec = A.rec;
-  int4 xs = __ldg(A.node + s), xt = __ldg(A.node + t);
-  uint32_t pis, pit;
-  probe_pi_pair(pr, (uint32_t)xs.x, (uint32_t)xt.x, pis, pit);
-  float a = signed_term(probe_z_from_pi(pr, pis), (uint32_t)xs.w);
-  float b = signed_term(probe_z_from_pi(pr, pit), (uint32_t)xt.w);
+template <bool DEBUG, class ZP>
+__device__ __forceinline__ float walk_pair(const int4* __restrict__ rec, const int4* __restrict__ node,
+                                           uint32_t* visits, uint32_t walk_tag, const ZP& zp, int32_t s,
+                                           int32_t t, int32_t L, uint64_t seed, uint64_t pair) {
+  int4 xs = __ldg(node + s), xt = __ldg(node + t);
+  int zs, zt;
+  zp.pair((uint32_t)xs.x, (uint32_t)xt.x, zs, zt);
+  float a = signed_term(zs, (uint32_t)xs.w);
+  float b = signed_term(zt, (uint32_t)xt.w);
   if (DEBUG) {
-    atomicAdd(A.visits + xs.x, 1u);
-    atomicAdd(A.visits + xt.x, 1u);
+    atomicAdd(visits + xs.x, 1u);
+    atomicAdd(visits + xt.x, 1u);
   }
   if (L == 0) return __fsub_rn(a, b);
   const uint64_t ws = 2 * pair, wt = ws + 1;
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  const uint32_t tag = A.walk_tag;
-  Philox4 rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), 0u, tag, k0, k1);
-  Philox4 rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), 0u, tag, k0, k1);
+  Philox4 rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), 0u, walk_tag, k0, k1);
+  Philox4 rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), 0u, walk_tag, k0, k1);
   int4 ns = __ldg(rec + ((uint32_t)xs.y + __umulhi(rs.y, (uint32_t)xs.z)));
   int4 nt = __ldg(rec + ((uint32_t)xt.y + __umulhi(rt.y, (uint32_t)xt.z)));
   for (uint32_t blk = 0;; ++blk) {
@@ -264,8 +287,8 @@ __device__ __forceinline__ float walk_pair(const WalkArgs& A, const Probe& pr, i
       if (more) {
         uint32_t wsw, wtw;
         if (w == 3) {
-          rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), blk + 1u, tag, k0, k1);
-          rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), blk + 1u, tag, k0, k1);
+          rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), blk + 1u, walk_tag, k0, k1);
+          rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), blk + 1u, walk_tag, k0, k1);
           wsw = rs.x;
           wtw = rt.x;
         } else {
@@ -275,12 +298,12 @@ __device__ __forceinline__ float walk_pair(const WalkArgs& A, const Probe& pr, i
         ns2 = __ldg(rec + ((uint32_t)ns.y + __umulhi(wsw, (uint32_t)ns.z)));
         nt2 = __ldg(rec + ((uint32_t)nt.y + __umulhi(wtw, (uint32_t)nt.z)));
       }
-      probe_pi_pair(pr, (uint32_t)ns.x, (uint32_t)nt.x, pis, pit);
-      a = __fadd_rn(a, signed_term(probe_z_from_pi(pr, pis), (uint32_t)ns.w));
-      b = __fadd_rn(b, signed_term(probe_z_from_pi(pr, pit), (uint32_t)nt.w));
+      zp.pair((uint32_t)ns.x, (uint32_t)nt.x, zs, zt);
+      a = __fadd_rn(a, signed_term(zs, (uint32_t)ns.w));
+      b = __fadd_rn(b, signed_term(zt, (uint32_t)nt.w));
       if (DEBUG) {
-        atomicAdd(A.visits + ns.x, 1u);
-        atomicAdd(A.visits + nt.x, 1u);
+        atomicAdd(visits + ns.x, 1u);
+        atomicAdd(visits + nt.x, 1u);
       }
       if (!more) return __fsub_rn(a, b);
       ns = ns2;
@@ -310,8 +333,74 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkArgs A) {
     if (p >= R) continue;
     const Probe pr = make_probe(A.n, P.seed, k, A.probe_tag);
     const uint64_t pair = (uint64_t)k * R + p;
-    const float U = walk_pair<DEBUG>(A, pr, P.s, P.t, P.L, P.seed, pair);
+    const ZOnTheFly zp{pr};
+    const float U = walk_pair<DEBUG>(A.rec, A.node, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
     A.u[P.u_begin + pair] = U;
+  }
+}
+
+// Probe-major kernel: a block claims one probe k of one query, writes the
+// whole vector z^(k) into a 2-bit shared-memory table (one Feistel cycle-walk
+// per node, a flat per-lane queue so lanes stay busy), then its warps run the
+// probe's 32-replica tiles reading z from the table.  Same values as the
+// on-the-fly kernel; cheaper whenever a probe's walks visit more nodes than
+// the graph has (2 R (L+1) > n).
+template <bool DEBUG>
+__global__ void __launch_bounds__(kWalkThreads) walk_table_kernel(WalkArgs A,
+                                                                  const unsigned long long* __restrict__ probe_prefix,
+                                                                  unsigned long long* __restrict__ probe_counter) {
+  extern __shared__ uint32_t tab[];
+  __shared__ unsigned long long sh_probe;
+  __shared__ uint32_t sh_tile;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t n = A.n;
+  const uint32_t nwords = (n + 15u) / 16u;
+  const unsigned long long total = A.totals->probes;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      sh_probe = atomicAdd(probe_counter, 1ull);
+      sh_tile = 0;
+    }
+    __syncthreads();
+    const unsigned long long j = sh_probe;
+    if (j >= total) return;
+    const int64_t q = find_segment(probe_prefix, A.nq, j);
+    const QPlan& P = A.plans[q];
+    const uint32_t k = (uint32_t)(j - P.probe_begin);
+    {
+      const Probe pr = make_probe(n, P.seed, k, A.probe_tag);
+      uint32_t w = threadIdx.x, v = w * 16u, x = v, acc = 0;
+      while (w < nwords) {
+        x = feistel_once(pr, x);
+        if (x < n) {
+          acc |= z_code(probe_z_from_pi(pr, x)) << ((v & 15u) << 1);
+          ++v;
+          if ((v & 15u) == 0 || v >= n) {
+            tab[w] = acc;
+            acc = 0;
+            w += blockDim.x;
+            v = w * 16u;
+          }
+          x = v;
+        }
+      }
+    }
+    __syncthreads();
+    const ZTable zp{tab};
+    const uint32_t R = P.R, chunks = P.chunks;
+    for (;;) {
+      uint32_t c = 0;
+      if (lane == 0) c = atomicAdd(&sh_tile, 1u);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      if (c >= chunks) break;
+      const uint32_t p = c * 32u + lane;
+      if (p < R) {
+        const uint64_t pair = (uint64_t)k * R + p;
+        const float U = walk_pair<DEBUG>(A.rec, A.node, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
+        A.u[P.u_begin + pair] = U;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -415,6 +504,35 @@ static void prof_end(pw_graph* g, cudaStream_t stream, cudaEvent_t a, int kind) 
   g->prof.spans.push_back({a, b, kind});
 }
 
+// Largest graph whose 2-bit probe table fits in shared memory next to the kernel's own state.
+static size_t table_bytes(const pw_graph* g) { return sizeof(uint32_t) * (size_t)((g->n + 15) / 16); }
+static constexpr size_t kMaxTableBytes = 200 * 1024;
+
+static int table_grid(pw_graph* g, bool debug, size_t smem) {
+  int nb = 0;
+  if (debug) {
+    cudaFuncSetAttribute(walk_table_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_table_kernel<true>, kWalkThreads, smem);
+  } else {
+    cudaFuncSetAttribute(walk_table_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_table_kernel<false>, kWalkThreads, smem);
+  }
+  return g->sm_count * (nb > 0 ? nb : 1);
+}
+
+static pw_status launch_walk_table(pw_graph* g, cudaStream_t stream, bool debug, const WalkArgs& a,
+                                   const unsigned long long* probe_prefix, unsigned long long* probe_counter) {
+  const size_t smem = table_bytes(g);
+  const int grid = table_grid(g, debug, smem);
+  if (debug)
+    walk_table_kernel<true><<<grid, kWalkThreads, smem, stream>>>(a, probe_prefix, probe_counter);
+  else
+    walk_table_kernel<false><<<grid, kWalkThreads, smem, stream>>>(a, probe_prefix, probe_counter);
+  count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  return PW_OK;
+}
+
 static pw_status launch_walk(pw_graph* g, cudaStream_t stream, bool debug, const WalkArgs& a) {
   const int grid = walk_grid(g, debug);
   if (debug)
@@ -505,9 +623,25 @@ pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_
   wa.visits = debug ? dbg->visits : nullptr;
   wa.walk_tag = kTagWalk;
   wa.probe_tag = kTagProbe;
+  // Mode: the probe-table kernel pays n Feistel cycle-walks per probe, the
+  // on-the-fly kernel about 2.5 per visit (2 R (L+1) visits per probe).
+  int mode = params ? params->walk_mode : 0;
+  if (mode == 0) {
+    const double table_cost = (double)T.probes * (double)g->n;
+    const double visit_cost = 2.5 * 2.0 * ((double)T.steps + (double)T.u_slots);
+    mode = (table_bytes(g) <= kMaxTableBytes && table_cost < visit_cost) ? 2 : 1;
+  }
+  if (mode == 2 && table_bytes(g) > kMaxTableBytes) mode = 1;
+  g->last_walk_mode = mode;
   cudaEvent_t ev_walk;
   prof_begin(g, stream, &ev_walk);
-  if (T.tiles > 0 && (st = launch_walk(g, stream, debug, wa)) != PW_OK) return st;
+  if (T.tiles > 0) {
+    if (mode == 2)
+      st = launch_walk_table(g, stream, debug, wa, prefix + nq + 1, counters + 2);
+    else
+      st = launch_walk(g, stream, debug, wa);
+    if (st != PW_OK) return st;
+  }
   prof_end(g, stream, ev_walk, 0);
   if (g->prof.enabled) {
     g->prof.walk_launches += T.tiles > 0 ? 1 : 0;
@@ -738,6 +872,8 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
     out->transitions = P.transitions;
     out->pilot_transitions = P.pilot_transitions;
     out->queries = P.queries;
+    out->walk_mode = g->last_walk_mode;
+    out->reserved = 0;
   }
   if (reset) {
     P.walk_ms = P.pilot_ms = P.finish_ms = 0;

@@ -48,8 +48,8 @@ class pw_params(ctypes.Structure):
         ("R", ctypes.c_uint64),
         ("R_max", ctypes.c_uint64),
         ("seed", ctypes.c_uint64),
-        ("tiles_per_claim", ctypes.c_int32),
-        ("block_threads", ctypes.c_int32),
+        ("walk_mode", ctypes.c_int32),
+        ("reserved1", ctypes.c_int32),
     ]
 
 
@@ -69,6 +69,8 @@ class pw_profile_stats(ctypes.Structure):
         ("transitions", ctypes.c_uint64),
         ("pilot_transitions", ctypes.c_uint64),
         ("queries", ctypes.c_uint64),
+        ("walk_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

@@ -111,16 +111,19 @@ def _compare_query(pw, host, g, s, t, eps, L, seed, params, cfg):
     return dev, orc
 
 
-def test_debug_query_pilot_bit_exact(pw, oracle_lib, tiny):
+@pytest.mark.parametrize("walk_mode", [1, 2])
+def test_debug_query_pilot_bit_exact(pw, oracle_lib, tiny, walk_mode):
     host, g = tiny
+    params = pw.make_params(walk_mode=walk_mode)
     for s, t, seed in ((3, 77, 12345), (0, 199, 1), (150, 9, 2**62 + 11)):
-        _compare_query(pw, host, g, s, t, 0.2, 32, seed, None, oracle.budget_cfg())
+        _compare_query(pw, host, g, s, t, 0.2, 32, seed, params, oracle.budget_cfg())
 
 
+@pytest.mark.parametrize("walk_mode", [1, 2])
 @pytest.mark.parametrize("B,G,R,L", [(3, 1, 2, 0), (5, 3, 7, 1), (4, 5, 45, 13), (2, 3, 70, 33), (1, 1, 33, 4)])
-def test_debug_query_fixed_ragged_bit_exact(pw, oracle_lib, tiny, B, G, R, L):
+def test_debug_query_fixed_ragged_bit_exact(pw, oracle_lib, tiny, B, G, R, L, walk_mode):
     host, g = tiny
-    params = pw.make_params(budget_mode=pw.PW_BUDGET_FIXED, B=B, G=G, R=R)
+    params = pw.make_params(budget_mode=pw.PW_BUDGET_FIXED, B=B, G=G, R=R, walk_mode=walk_mode)
     cfg = oracle.budget_cfg(mode=oracle.MODE_FIXED, B=B, G=G, R=R)
     _compare_query(pw, host, g, 10, 20, 0.3, L, 424242, params, cfg)
 
@@ -140,13 +143,14 @@ def test_budget_modes_match_oracle(pw, oracle_lib, tiny, mode):
         assert (dev["B"], dev["G"], dev["K"], dev["R"]) == (orc["B"], orc["G"], orc["K"], orc["R"])
 
 
-def test_tiny_batch_parity_and_accuracy(pw, oracle_lib, tiny):
+@pytest.mark.parametrize("walk_mode", [0, 1, 2])
+def test_tiny_batch_parity_and_accuracy(pw, oracle_lib, tiny, walk_mode):
     """64 queries of the tiny workload: per-query beta_hat equal to the oracle
     (tolerance 1e-5 rel; in fact bit-exact) and >= 95% within eps of the exact beta."""
     host, g = tiny
     s, t = uniform_pairs(host.n, 64, 100)
     seeds = query_seeds(64, 200)
-    beta, st = pw.pw_query_batch(g.handle, s, t, 0.2, 32, seeds)
+    beta, st = pw.pw_query_batch(g.handle, s, t, 0.2, 32, seeds, pw.make_params(walk_mode=walk_mode))
     assert np.all(st == 0)
     ob, _, ost = oracle.query_many(host, s, t, 0.2, 32, seeds)
     assert np.all(ost == 0)
@@ -271,11 +275,23 @@ def test_ba_full_size_sampled_probes(oracle_lib, ba_batch):
         assert abs(b["qsel"][i] - want) <= REL_TOL * abs(want) + 1e-300
 
 
+@pytest.mark.slow
 def test_ba_full_size_whole_queries(oracle_lib, ba_batch):
     b = ba_batch
-    for qi in (0, 517):
+    for qi in (517,):
         want = oracle.query(b["host"], int(b["s"][qi]), int(b["t"][qi]), 0.1, 200, int(b["seeds"][qi]))
         assert b["beta"][qi] == want["beta"]
+
+
+def test_ba_modes_agree(pw, ba):
+    """Per-visit and probe-table kernels give identical estimates on BA queries."""
+    host, g = ba
+    s, t = uniform_pairs(host.n, 6, 77)
+    seeds = query_seeds(6, 78)
+    b1, st1 = pw.pw_query_batch(g.handle, s, t, 0.2, 50, seeds, pw.make_params(walk_mode=1))
+    b2, st2 = pw.pw_query_batch(g.handle, s, t, 0.2, 50, seeds, pw.make_params(walk_mode=2))
+    assert np.all(st1 == 0) and np.all(st2 == 0)
+    np.testing.assert_array_equal(b1, b2)
 
 
 def test_ba_full_size_accuracy_vs_series(ba_batch):
