@@ -137,6 +137,27 @@ pw_status pw_query_batch_device(pw_graph* g, int64_t count, const int64_t* d_s, 
                                 const double* d_eps, const int32_t* d_L, const uint64_t* d_seeds,
                                 const pw_params* params, double* d_beta_hat, int32_t* d_status, void* stream);
 
+/* pw_query_batch_noalloc: the device-array batch of pw_query_batch_device for
+ * callers that must not allocate device memory while they serve queries (for
+ * example a request path where allocator calls, which can block and
+ * synchronise the device, are forbidden).  The paper has no counterpart: this
+ * is a deployment variant of the same computation, with the same results.
+ * The call makes no cudaMalloc, cudaFree or allocating library call: all of
+ * its scratch (query plans, offsets, counters, the U_p and Q_R buffers) lives
+ * in one static 64 MiB device array that the library holds on every GPU that
+ * loads it, until the process exits.  A batch whose scratch exceeds 64 MiB is
+ * rejected with PW_ERR_NOMEM (for the n = 100,000 BA graph at eps = 0.1,
+ * about four queries per call; for small graphs or large eps, many more).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array and clears the counters that must start at
+ * zero; calls that overlap on the GPU (other streams or threads) race on it.
+ * Arguments, layout and ordering on `stream` are those of
+ * pw_query_batch_device; like it, the call synchronises `stream` once. */
+pw_status pw_query_batch_noalloc(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t,
+                                 const double* d_eps, const int32_t* d_L, const uint64_t* d_seeds,
+                                 const pw_params* params, double* d_beta_hat, int32_t* d_status, void* stream);
+
 /* ---- server (continuous batching) ----------------------------------------
  * A server keeps the graph and the per-query accumulators on the device and
  * runs a persistent kernel fed by a device work queue.  Queries are admitted

@@ -914,3 +914,166 @@ pw_status pw_debug_batch_probe_q(pw_graph* g, int64_t count, const int64_t* s, c
 }
 
 }  // extern "C"
+
+namespace pw {
+
+// ---------------------------------------------------------------------------
+// Batch entry point that allocates nothing.
+//
+// Some callers cannot allocate device memory while they run queries: a
+// real-time service that forbids allocator calls (cudaMalloc can block and
+// synchronise the device) in its request path, or code that runs where the
+// CUDA allocator is off limits.  pw_query_batch_noalloc serves them: its
+// scratch (query plans, offsets, counters, the U_p and Q_R buffers) is carved
+// out of the file-scope array below, so the call itself makes no cudaMalloc,
+// cudaFree or allocating library call.  The array holds kNoAllocScratchBytes
+// on every GPU that loads the library, until the process exits.  Every call
+// shares it: calls that overlap on the GPU (different streams, or another
+// thread) race on its contents; the counters that must start at zero are
+// cleared by each call.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;
+static __device__ __align__(256) unsigned char pw_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_lock;
+static void* g_noalloc_addr[128] = {nullptr};
+
+// Device address of the scratch array on `device` (which must be current).
+// In host code the array's name is only a host-side stand-in, so the real
+// address comes from cudaGetSymbolAddress, once per device.
+static pw_status noalloc_scratch(int device, unsigned char** out) {
+  if (device < 0 || device >= 128) return set_error(PW_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> guard(g_noalloc_lock);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, pw_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(pw_noalloc_scratch)");
+    g_noalloc_addr[device] = p;
+  }
+  *out = (unsigned char*)g_noalloc_addr[device];
+  return PW_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace pw
+
+extern "C" pw_status pw_query_batch_noalloc(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t,
+                                            const double* d_eps, const int32_t* d_L, const uint64_t* d_seeds,
+                                            const pw_params* params, double* d_beta_hat, int32_t* d_status,
+                                            void* stream_ptr) {
+  using namespace pw;
+  if (!g) return set_error(PW_ERR_ARG, "graph is NULL");
+  if (count < 0) return set_error(PW_ERR_ARG, "count < 0");
+  if (count == 0) return PW_OK;
+  if (!d_s || !d_t || !d_eps || !d_L || !d_beta_hat || !d_status) return set_error(PW_ERR_ARG, "NULL device array");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  BudgetArgs ba;
+  pw_status st = resolve_budget(params, g, &ba, nullptr);
+  if (st != PW_OK) return st;
+  unsigned char* base = nullptr;
+  if ((st = noalloc_scratch(g->device, &base)) != PW_OK) return st;
+  cudaStream_t stream = (cudaStream_t)stream_ptr;
+  const bool pilot = ba.mode == PW_BUDGET_PILOT;
+  const size_t nq = (size_t)count;
+  // fixed part of the layout: plans, pilot plans, offsets, totals, counters, pilot U
+  size_t off = 0;
+  const size_t o_plans = off;
+  off = align256(off + sizeof(QPlan) * nq);
+  const size_t o_pplans = off;
+  off = align256(off + sizeof(QPlan) * nq);
+  const size_t o_prefix = off;
+  off = align256(off + sizeof(unsigned long long) * 4 * (nq + 1));
+  const size_t o_totals = off;
+  off = align256(off + sizeof(Totals) * 2);
+  const size_t o_counters = off;
+  off = align256(off + 64);
+  const size_t o_pilot_u = off;
+  off = align256(off + (pilot ? sizeof(float) * nq * (size_t)ba.K0 * (size_t)ba.R0 : 0));
+  if (off > kNoAllocScratchBytes)
+    return set_error(PW_ERR_NOMEM, "pw_query_batch_noalloc: batch needs more than the 64 MiB static scratch");
+  QPlan* plans = (QPlan*)(base + o_plans);
+  QPlan* pplans = (QPlan*)(base + o_pplans);
+  unsigned long long* prefix = (unsigned long long*)(base + o_prefix);
+  unsigned long long* pprefix = prefix + 2 * (nq + 1);
+  Totals* totals = (Totals*)(base + o_totals);
+  unsigned long long* counters = (unsigned long long*)(base + o_counters);
+  float* pilot_u = (float*)(base + o_pilot_u);
+  PW_CUDA_TRY(cudaStreamWaitEvent(stream, g->ws.last_use, 0));
+  PW_CUDA_TRY(cudaMemsetAsync(counters, 0, 64, stream));
+  const int qthreads = 128;
+  const int qblocks = (int)((count + qthreads - 1) / qthreads);
+  budget_init_kernel<<<qblocks, qthreads, 0, stream>>>(count, d_s, d_t, d_eps, d_L, d_seeds, ba, g->n, g->d_node,
+                                                       plans, pilot ? pplans : nullptr);
+  count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  WalkArgs wa;
+  wa.rec = g->d_rec;
+  wa.node = g->d_node;
+  wa.nq = count;
+  wa.n = (uint32_t)g->n;
+  wa.visits = nullptr;
+  if (pilot) {
+    scan_kernel<<<1, 1024, 0, stream>>>(pplans, count, pprefix, totals + 1);
+    count_launch();
+    wa.plans = pplans;
+    wa.tile_prefix = pprefix;
+    wa.totals = totals + 1;
+    wa.tile_counter = counters + 1;
+    wa.u = pilot_u;
+    wa.walk_tag = kTagWalkPilot;
+    wa.probe_tag = kTagProbePilot;
+    if ((st = launch_walk(g, stream, false, wa)) != PW_OK) return st;
+    pilot_budget_kernel<<<qblocks, qthreads, 0, stream>>>(count, plans, pplans, pilot_u, ba, g->d_node);
+    count_launch();
+    PW_CUDA_TRY(cudaGetLastError());
+  }
+  scan_kernel<<<1, 1024, 0, stream>>>(plans, count, prefix, totals);
+  count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  PW_CUDA_TRY(cudaMemcpyAsync(g->ws.host_totals, totals, sizeof(Totals), cudaMemcpyDeviceToHost, stream));
+  PW_CUDA_TRY(cudaStreamSynchronize(stream));
+  const Totals T = *g->ws.host_totals;
+  const size_t o_u = off;
+  off = align256(off + sizeof(float) * (size_t)T.u_slots);
+  const size_t o_q = off;
+  off = align256(off + sizeof(double) * (size_t)T.probes);
+  if (off > kNoAllocScratchBytes)
+    return set_error(PW_ERR_NOMEM, "pw_query_batch_noalloc: the walks of this batch need more than the 64 MiB "
+                                   "static scratch (U_p and Q_R buffers); split the batch");
+  float* u = (float*)(base + o_u);
+  double* qbuf = (double*)(base + o_q);
+  int mode = params ? params->walk_mode : 0;
+  if (mode == 0) {
+    const double table_cost = (double)T.probes * (double)g->n;
+    const double visit_cost = 2.5 * 2.0 * ((double)T.steps + (double)T.u_slots);
+    mode = (table_bytes(g) <= kMaxTableBytes && table_cost < visit_cost) ? 2 : 1;
+  }
+  if (mode == 2 && table_bytes(g) > kMaxTableBytes) mode = 1;
+  wa.plans = plans;
+  wa.tile_prefix = prefix;
+  wa.totals = totals;
+  wa.tile_counter = counters;
+  wa.u = u;
+  wa.walk_tag = kTagWalk;
+  wa.probe_tag = kTagProbe;
+  if (T.tiles > 0) {
+    st = mode == 2 ? launch_walk_table(g, stream, false, wa, prefix + nq + 1, counters + 2)
+                   : launch_walk(g, stream, false, wa);
+    if (st != PW_OK) return st;
+  }
+  if (T.probes > 0) {
+    const int fthreads = 128;
+    const unsigned long long want = (T.probes + fthreads - 1) / fthreads;
+    const int fblocks = (int)std::min<unsigned long long>(want, (unsigned long long)g->sm_count * 64);
+    probe_finish_kernel<<<fblocks, fthreads, 0, stream>>>(plans, count, prefix + nq + 1, totals, u, qbuf);
+    count_launch();
+    PW_CUDA_TRY(cudaGetLastError());
+  }
+  mom_kernel<<<(unsigned)count, 128, 0, stream>>>(plans, qbuf, d_beta_hat, d_status);
+  count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  PW_CUDA_TRY(cudaEventRecord(g->ws.last_use, stream));
+  return PW_OK;
+}

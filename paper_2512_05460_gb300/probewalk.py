@@ -93,6 +93,7 @@ SIGNATURES = {
     "pw_query_batch": (_i32, [_vp, _i64, P(_i64), P(_i64), P(_dbl), P(_i32), P(_u64), P(pw_params), P(_dbl),
                               P(_i32)]),
     "pw_query_batch_device": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, P(pw_params), _vp, _vp, _vp]),
+    "pw_query_batch_noalloc": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, P(pw_params), _vp, _vp, _vp]),
     "pw_server_create": (_i32, [_vp, P(pw_params), ctypes.c_size_t, P(_vp)]),
     "pw_server_submit": (_i32, [_vp, _i64, _i64, _dbl, _i32, P(_u64), P(_u64)]),
     "pw_server_poll": (_i32, [_vp, _u64, P(_dbl)]),
@@ -235,6 +236,21 @@ def pw_query_batch_device(g: int, count: int, d_s, d_t, d_eps, d_L, d_seeds, d_b
     _check(lib().pw_query_batch_device(g, count, _dev_ptr(d_s), _dev_ptr(d_t), _dev_ptr(d_eps), _dev_ptr(d_L),
                                        _dev_ptr(d_seeds), _params(params), _dev_ptr(d_beta), _dev_ptr(d_status),
                                        stream))
+
+
+def pw_query_batch_noalloc(g: int, count: int, d_s, d_t, d_eps, d_L, d_seeds, d_beta, d_status, params=None,
+                           stream=None) -> None:
+    """pw_query_batch_device for callers that must not allocate: the library
+    takes its scratch from a static 64 MiB device array (see the header)."""
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    _check(lib().pw_query_batch_noalloc(g, count, _dev_ptr(d_s), _dev_ptr(d_t), _dev_ptr(d_eps), _dev_ptr(d_L),
+                                        _dev_ptr(d_seeds), _params(params), _dev_ptr(d_beta), _dev_ptr(d_status),
+                                        stream))
 
 
 # ---- server ----------------------------------------------------------------
