@@ -39,6 +39,12 @@ WORKLOADS = {
 }
 
 SECTOR_BYTES = 32  # one 16-byte neighbour record per transition lives in one 32-byte sector
+L2_BYTES = 129 << 20
+WALK_KERNEL_NAME = {1: "walk_kernel (per-visit probe evaluation)", 2: "walk_table_kernel (per-probe table)"}
+# DRAM bytes per launch of the walk kernel from the committed ncu capture
+# (profiles/), scaled from the captured case to the full launch by transitions;
+# None until a capture of the current kernel exists.
+WALK_TRAFFIC: dict = {}
 
 
 def load_peaks():
@@ -198,7 +204,7 @@ def run_reference(args, wl, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {wl['desc']}; {wl['queries']} uniform pairs; L={wl['L']}; "
-                                   f"eps={wl['eps']}; delta=0.01; PILOT budget", "l2": "n/a (CPU)"},
+                                   f"eps={wl['eps']}; delta=0.01; PILOT budget c_B=0.5", "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -299,14 +305,27 @@ def run_ours(args, wl, world, rank, local):
     plain_qps = plain_n / sum(lat) if lat else None
 
     # ---- roofline of the walk kernel -----------------------------------------
+    # Algorithmic bytes: one 32-byte sector (holding the 16-byte neighbour
+    # record) per walk transition.  Records larger than L2 are bound by HBM
+    # (MEASURED_PEAKS.json); an L2-resident record array (this BA graph: 16 MB)
+    # is bound by L2 sector throughput, measured here by dependent random
+    # gathers over the same array.
     hbm_peak, peak_kind = load_peaks()
     walk_bytes = transitions_per_step * SECTOR_BYTES
     achieved = walk_bytes / (walk_ms_avg / 1000.0) / 1e9 if walk_ms_avg > 0 else 0.0
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "kernel": "walk_kernel",
-                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": walk_bytes,
-                "bytes_model": "32 B (one sector holding the 16 B neighbour record) per walk transition",
-                "walk_ms_per_launch": walk_ms_avg}
+    record_bytes = 16 * host.nnz
+    if record_bytes < L2_BYTES // 2:
+        l2_peak = pw.pw_debug_gather_peak(g.handle, 2048) * SECTOR_BYTES / 1e9
+        roofline = {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
+                    "peak_kind": "measured in this run: dependent random 16-B gathers over the same record array "
+                                 "(pw_debug_gather_peak)"}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "peak_kind": peak_kind}
+    roofline.update({"traffic": WALK_TRAFFIC.get((args.workload, walk_mode)), "kernel": WALK_KERNEL_NAME[walk_mode],
+                     "algorithmic_bytes_per_launch": walk_bytes,
+                     "bytes_model": "32 B (one sector holding the 16 B neighbour record) per walk transition",
+                     "walk_ms_per_launch": walk_ms_avg})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -328,7 +347,7 @@ def run_ours(args, wl, world, rank, local):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {wl['desc']}; {nq} uniform pairs per GPU; L={wl['L']}; "
-                                   f"eps={wl['eps']}; delta=0.01; PILOT budget c_B={args.c_B or 1.0}",
+                                   f"eps={wl['eps']}; delta=0.01; PILOT budget c_B={args.c_B or 0.5}",
                        "queries_per_gpu": nq, "L": wl["L"], "eps": wl["eps"],
                        "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                        "parallelism": f"query sharding x{world}"},

@@ -52,7 +52,9 @@ typedef enum {
 /* Budget modes.  THEORY is Algorithm 1's parameter line (Eqs. B-value,
  * G-value, R-value, K-value).  The paper's experiments do not state the K and
  * R they used; SCALED scales THEORY's B and R by c_B and c_R; FIXED takes B, G,
- * R as given; PILOT (default) keeps G, takes B = ceil(c_B / eps^2) and sets R
+ * R as given; PILOT (default) keeps G, takes B = ceil(c_B / eps^2)
+ * (c_B = 0.5 by default: the smallest of {0.25, 0.5, 1, 2, 4} that kept >= 95% of
+ * held-out queries within eps on the tiny and BA workloads) and sets R
  * from Lemma 3.7's sufficient condition R >= 4 sigma^2 / theta, with sigma^2 and
  * theta estimated by a pilot of K0 probes x R0 replicas on reserved streams
  * (theta floored by theta_0 = (1/8)(1 - eps/2)(1/d_s + 1/d_t)^2 from the proof of
@@ -66,7 +68,7 @@ typedef struct pw_params {
   int32_t pilot_K0;        /* PILOT probes; 0 -> 64 */
   int32_t pilot_R0;        /* PILOT replicas per probe, 2..32; 0 -> 32 */
   int32_t reserved0;
-  double c_B;              /* 0 -> 1.0 */
+  double c_B;              /* 0 -> 0.5 in PILOT mode (calibrated), 1.0 otherwise */
   double c_R;              /* 0 -> 1.0 */
   uint64_t B, G, R;        /* FIXED mode values (B >= 1, G >= 1, R >= 2) */
   uint64_t R_max;          /* PILOT / SCALED clamp; 0 -> 4096 */
@@ -180,6 +182,12 @@ pw_status pw_debug_philox(pw_graph* g, const uint32_t* ctr, const uint32_t* key,
  * n) of probe k under stream tag `tag` (3 main, 4 pilot) of the query keyed by
  * seed; returns the parity parameter r in *r (host, may be NULL). */
 pw_status pw_debug_probe(pw_graph* g, uint64_t seed, uint32_t k, uint32_t tag, int8_t* z, int32_t* r);
+/* pw_debug_gather_peak: sector-throughput ceiling of the walk's memory side on
+ * this graph: dependent random 16-byte gathers over the graph's record array
+ * (8 chains per thread, full occupancy, no other work), best of 3 launches of
+ * `iters` gathers per chain; *sectors_per_s (host) receives gathers/s, each
+ * gather reading one 32-byte sector. */
+pw_status pw_debug_gather_peak(pw_graph* g, int32_t iters, double* sectors_per_s);
 /* pw_debug_walk: trajectory X_0..X_L (host int64 array of L+1) of walk
  * `walk_id` under stream tag `tag` (1 main, 2 pilot). */
 pw_status pw_debug_walk(pw_graph* g, int64_t start, int32_t L, uint64_t seed, uint64_t walk_id, uint32_t tag,

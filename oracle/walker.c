@@ -268,7 +268,9 @@ static void fill_defaults(const orc_budget_cfg* in, orc_budget_cfg* c) {
   if (c->R0 <= 1) c->R0 = 32;
   if (c->R_max == 0) c->R_max = 4096;
   if (!(c->c_R > 0)) c->c_R = 1.0;
-  if (!(c->c_B > 0)) c->c_B = (c->mode == ORC_PILOT) ? 1.0 : 1.0;
+  /* PILOT's c_B default (0.5) is the calibrated reading of the experimental
+   * budget, which the paper leaves open; SCALED scales Eq. B-value by c_B = 1. */
+  if (!(c->c_B > 0)) c->c_B = (c->mode == ORC_PILOT) ? 0.5 : 1.0;
 }
 
 /* R of Eq. R-value before the ceiling. */

@@ -53,6 +53,39 @@ __host__ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t 
   return Philox4{c0, c1, c2, c3};
 }
 
+// Round keys of one query key, hoisted out of the walk loop (the key schedule
+// is the same for every counter of the query).
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+
+__host__ __device__ __forceinline__ PhiloxKeys philox_keys(uint64_t seed) {
+  PhiloxKeys K;
+  uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    K.k0[r] = a;
+    K.k1[r] = b;
+    a += kPhiloxW0;
+    b += kPhiloxW1;
+  }
+  return K;
+}
+
+__host__ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                           const PhiloxKeys& K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = mulhi32(kPhiloxM0, c0), lo0 = kPhiloxM0 * c0;
+    const uint32_t hi1 = mulhi32(kPhiloxM1, c2), lo1 = kPhiloxM1 * c2;
+    c0 = hi1 ^ c1 ^ K.k0[r];
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ K.k1[r];
+    c3 = lo0;
+  }
+  return Philox4{c0, c1, c2, c3};
+}
+
 __host__ __device__ __forceinline__ Philox4 philox_seeded(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
                                                            uint32_t c3) {
   return philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
@@ -115,6 +148,7 @@ __host__ __device__ __forceinline__ Probe make_probe(uint32_t n, uint64_t seed, 
   return P;
 }
 
+// Round function: top h bits of ((x ^ key) * C1, xor-folded by 16, * C2).
 __host__ __device__ __forceinline__ uint32_t feistel_f(uint32_t x, uint32_t key, uint32_t h) {
   uint32_t y = (x ^ key) * 0x9E3779B1u;
   y ^= y >> 16;

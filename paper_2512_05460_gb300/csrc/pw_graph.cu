@@ -58,6 +58,27 @@ __global__ void debug_walk_kernel(const int4* __restrict__ rec, const int4* __re
   }
 }
 
+// Sector-throughput ceiling of the walk's memory side: dependent random 16-B
+// gathers over the graph's own record array (the next index depends on the
+// loaded value, as in a walk), 8 independent chains per thread, no other work.
+__global__ void __launch_bounds__(256) gather_peak_kernel(const int4* __restrict__ rec, uint32_t nnz, uint32_t iters,
+                                                         uint32_t* sink) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = (tid * 8u + (uint32_t)j) * 0x9E3779B1u + 0x7F4A7C15u;
+  uint32_t acc = 0;
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int4 r = __ldg(rec + __umulhi(x[j], nnz));
+      x[j] = x[j] * 1664525u + 1013904223u + (uint32_t)r.y;
+      acc += (uint32_t)r.x;
+    }
+  }
+  if (acc == 0x12345678u) sink[0] = acc;
+}
+
 static pw_status validate_csr(int64_t n, const int64_t* rp, const int32_t* col, int64_t nnz, uint32_t flags,
                               int32_t* d_min, int32_t* d_max, int32_t* bipartite) {
   if (rp[0] != 0 || rp[n] != nnz) return set_error(PW_ERR_GRAPH, "row_ptr must start at 0 and end at nnz");
@@ -248,6 +269,39 @@ pw_status pw_debug_probe(pw_graph* g, uint64_t seed, uint32_t k, uint32_t tag, i
   PW_CUDA_TRY(cudaMemcpyAsync(&rr, d_r, sizeof rr, cudaMemcpyDeviceToHost, g->stream));
   PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
   if (r) *r = rr;
+  return PW_OK;
+}
+
+pw_status pw_debug_gather_peak(pw_graph* g, int32_t iters, double* sectors_per_s) {
+  if (!g || !sectors_per_s || iters < 1) return pw::set_error(PW_ERR_ARG, "NULL argument or iters < 1");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  pw::DeviceBuffer& b = g->ws.results;
+  pw_status st = pw::ensure_buffer(b, 64);
+  if (st != PW_OK) return st;
+  int nb = 0;
+  PW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pw::gather_peak_kernel, 256, 0));
+  const int blocks = g->sm_count * (nb > 0 ? nb : 1);
+  cudaEvent_t e0, e1;
+  PW_CUDA_TRY(cudaEventCreate(&e0));
+  PW_CUDA_TRY(cudaEventCreate(&e1));
+  double best = 0.0;
+  for (int rep = 0; rep < 3; ++rep) {
+    PW_CUDA_TRY(cudaEventRecord(e0, g->stream));
+    pw::gather_peak_kernel<<<blocks, 256, 0, g->stream>>>(g->d_rec, (uint32_t)g->nnz, (uint32_t)iters,
+                                                          (uint32_t*)b.ptr);
+    pw::count_launch();
+    PW_CUDA_TRY(cudaGetLastError());
+    PW_CUDA_TRY(cudaEventRecord(e1, g->stream));
+    PW_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    PW_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    const double rate = (double)blocks * 256.0 * 8.0 * (double)iters / (ms * 1e-3);
+    if (rate > best) best = rate;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *sectors_per_s = best;
   return PW_OK;
 }
 

@@ -241,13 +241,14 @@ struct ZOnTheFly {
   }
 };
 
-// Probe entries read from the block's 2-bit table of z^(k) (built once per probe).
+// Probe entries read from the block's 2-bit table of z^(k) (built once per
+// probe): code bit 0 = nonzero, bit 1 = negative.
 struct ZTable {
   const uint32_t* tab;
-  __device__ __forceinline__ static int decode(uint32_t c) { return c == 0 ? 0 : (c == 1 ? 1 : -1); }
+  __device__ __forceinline__ static int decode(uint32_t c) { return (int)(c & 1u) - (int)(c & 2u); }
   __device__ __forceinline__ void pair(uint32_t vs, uint32_t vt, int& zs, int& zt) const {
-    zs = decode((tab[vs >> 4] >> ((vs & 15u) << 1)) & 3u);
-    zt = decode((tab[vt >> 4] >> ((vt & 15u) << 1)) & 3u);
+    zs = decode(tab[vs >> 4] >> ((vs & 15u) << 1));
+    zt = decode(tab[vt >> 4] >> ((vt & 15u) << 1));
   }
 };
 
@@ -272,9 +273,9 @@ __device__ __forceinline__ float walk_pair(const int4* __restrict__ rec, const i
   }
   if (L == 0) return __fsub_rn(a, b);
   const uint64_t ws = 2 * pair, wt = ws + 1;
-  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  Philox4 rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), 0u, walk_tag, k0, k1);
-  Philox4 rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), 0u, walk_tag, k0, k1);
+  const PhiloxKeys keys = philox_keys(seed);
+  Philox4 rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), 0u, walk_tag, keys);
+  Philox4 rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), 0u, walk_tag, keys);
   int4 ns = __ldg(rec + ((uint32_t)xs.y + __umulhi(rs.y, (uint32_t)xs.z)));
   int4 nt = __ldg(rec + ((uint32_t)xt.y + __umulhi(rt.y, (uint32_t)xt.z)));
   for (uint32_t blk = 0;; ++blk) {
@@ -287,8 +288,8 @@ __device__ __forceinline__ float walk_pair(const int4* __restrict__ rec, const i
       if (more) {
         uint32_t wsw, wtw;
         if (w == 3) {
-          rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), blk + 1u, walk_tag, k0, k1);
-          rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), blk + 1u, walk_tag, k0, k1);
+          rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), blk + 1u, walk_tag, keys);
+          rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), blk + 1u, walk_tag, keys);
           wsw = rs.x;
           wtw = rt.x;
         } else {
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkArgs A) {
 // on-the-fly kernel; cheaper whenever a probe's walks visit more nodes than
 // the graph has (2 R (L+1) > n).
 template <bool DEBUG>
-__global__ void __launch_bounds__(kWalkThreads) walk_table_kernel(WalkArgs A,
+__global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A,
                                                                   const unsigned long long* __restrict__ probe_prefix,
                                                                   unsigned long long* __restrict__ probe_counter) {
   extern __shared__ uint32_t tab[];

@@ -102,6 +102,7 @@ SIGNATURES = {
     "pw_debug_philox": (_i32, [_vp, P(_u32), P(_u32), P(_u32)]),
     "pw_debug_probe": (_i32, [_vp, _u64, _u32, _u32, P(ctypes.c_int8), P(_i32)]),
     "pw_debug_walk": (_i32, [_vp, _i64, _i32, _u64, _u64, _u32, P(_i64)]),
+    "pw_debug_gather_peak": (_i32, [_vp, _i32, P(_dbl)]),
     "pw_debug_query": (_i32, [_vp, _i64, _i64, _dbl, _i32, P(_u64), P(pw_params), P(_dbl), P(_u64), P(_dbl),
                               P(_dbl), _i64, P(ctypes.c_float), _i64, P(_u32)]),
     "pw_debug_batch_probe_q": (_i32, [_vp, _i64, P(_i64), P(_i64), P(_dbl), P(_i32), P(_u64), P(pw_params), P(_dbl),
@@ -297,6 +298,13 @@ def pw_debug_probe(g: int, n: int, seed: int, k: int, tag: int = TAG_PROBE):
     r = _i32()
     _check(lib().pw_debug_probe(g, seed, k, tag, _p(z, ctypes.c_int8), ctypes.byref(r)))
     return z, r.value
+
+
+def pw_debug_gather_peak(g: int, iters: int = 2048) -> float:
+    """Sectors/s of dependent random 16-B gathers over the graph's records."""
+    out = _dbl()
+    _check(lib().pw_debug_gather_peak(g, iters, ctypes.byref(out)))
+    return out.value
 
 
 def pw_debug_walk(g: int, start: int, L: int, seed: int, walk_id: int, tag: int = TAG_WALK) -> np.ndarray:

@@ -256,8 +256,8 @@ def ba_batch(pw, ba):
     seeds = query_seeds(1000, 1001)
     rng = np.random.default_rng(3)
     sel_q = rng.integers(0, 1000, size=24)
-    # probe indices are drawn below K for every query (K = 3700 at eps = 0.1)
-    sel_k = rng.integers(0, 3700, size=24)
+    # probe indices are drawn below K for every query (K = 37 * ceil(0.5 / 0.1^2) = 1850)
+    sel_k = rng.integers(0, 1850, size=24)
     beta, st, KR, qsel = pw.pw_debug_batch_probe_q(g.handle, s, t, 0.1, 200, seeds, sel_q, sel_k)
     return dict(host=host, s=s, t=t, seeds=seeds, beta=beta, st=st, KR=KR, sel_q=sel_q, sel_k=sel_k, qsel=qsel)
 
@@ -265,11 +265,11 @@ def ba_batch(pw, ba):
 def test_ba_full_size_sampled_probes(oracle_lib, ba_batch):
     b = ba_batch
     assert np.all(b["st"] == 0)
-    assert np.all(b["KR"][:, 0] == 3700)
+    assert np.all(b["KR"][:, 0] == 1850)
     for i, (qi, k) in enumerate(zip(b["sel_q"], b["sel_k"])):
         R = int(b["KR"][qi, 1])
         budget = oracle.budget(b["host"], int(b["s"][qi]), int(b["t"][qi]), 0.1, 200, int(b["seeds"][qi]))
-        assert budget["R"] == R and budget["K"] == 3700
+        assert budget["R"] == R and budget["K"] == 1850
         want = oracle.probe_q(b["host"], int(b["s"][qi]), int(b["t"][qi]), 200, int(b["seeds"][qi]), R, [k])[0]
         assert b["qsel"][i] == want
         assert abs(b["qsel"][i] - want) <= REL_TOL * abs(want) + 1e-300

@@ -161,7 +161,7 @@ def test_scaled_and_fixed_budgets(oracle_lib):
 
 def test_pilot_budget_shape(oracle_lib, tiny_graph):
     got = oracle.budget(tiny_graph, 3, 77, 0.2, 32, 12345)
-    assert got["B"] == 25 and got["G"] == 37 and got["K"] == 925
+    assert got["B"] == 13 and got["G"] == 37 and got["K"] == 481  # ceil(0.5 / 0.2^2) = 13
     assert got["R"] % 32 == 0 and 32 <= got["R"] <= 4096
     d = tiny_graph.degrees
     theta0 = 0.125 * (1 - 0.1) * (1 / d[3] + 1 / d[77]) ** 2
