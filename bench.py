@@ -210,6 +210,53 @@ def run_reference(args, wl, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_server(pw, g, s, t, eps, L, seeds, params, want):
+    """pw_server_*: a burst of the whole batch (capacity; every estimate must
+    equal the batch entry point's), then Poisson arrivals at 0.5x and 0.9x of
+    that capacity.  Latency = submit to completion, measured by the server."""
+    from pw_inputs import poisson_arrivals
+
+    nq = s.size
+    srv = pw.pw_server_create(g.handle, params, 4 << 30)
+    out = {}
+    try:
+        t0 = time.perf_counter()
+        tickets = [pw.pw_server_submit(srv, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i]))
+                   for i in range(nq)]
+        pw.pw_server_drain(srv, 600000)
+        burst_s = time.perf_counter() - t0
+        tk, b, st, lat = pw.pw_server_collect(srv, 4 * nq)
+        order = {int(x): i for i, x in enumerate(tickets)}
+        got = np.empty(nq)
+        got[[order[int(x)] for x in tk]] = b
+        assert np.all(st == 0) and np.array_equal(got, want), "server estimates differ from the batch entry point"
+        cap_qps = nq / burst_s
+        out["burst"] = {"queries": nq, "queries_per_s": cap_qps, "p50_ms": float(np.percentile(lat, 50)),
+                        "p99_ms": float(np.percentile(lat, 99))}
+        loads = []
+        n_load = min(nq, 400)
+        for frac in (0.5, 0.9):
+            rate = frac * cap_qps
+            arr = poisson_arrivals(n_load, rate, 4242 + int(100 * frac))
+            t0 = time.perf_counter()
+            for i in range(n_load):
+                d = arr[i] - (time.perf_counter() - t0)
+                if d > 0:
+                    time.sleep(d)
+                pw.pw_server_submit(srv, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i]))
+            pw.pw_server_drain(srv, 600000)
+            wall = time.perf_counter() - t0
+            _, _, st, lat = pw.pw_server_collect(srv, 4 * nq)
+            assert np.all(st == 0)
+            loads.append({"offered_frac_of_capacity": frac, "offered_qps": rate, "achieved_qps": n_load / wall,
+                          "queries": n_load, "p50_ms": float(np.percentile(lat, 50)),
+                          "p99_ms": float(np.percentile(lat, 99))})
+        out["poisson"] = loads
+    finally:
+        pw.pw_server_destroy(srv)
+    return out
+
+
 def run_ours(args, wl, world, rank, local):
     import torch
 
@@ -304,6 +351,11 @@ def run_ours(args, wl, world, rank, local):
         lat.append(time.perf_counter() - t0)
     plain_qps = plain_n / sum(lat) if lat else None
 
+    # ---- continuous-batching server: burst capacity, then Poisson arrivals ----
+    server = None
+    if not args.no_server:
+        server = run_server(pw, g, s, t, eps, L, seeds, params, beta)
+
     # ---- roofline of the walk kernel -----------------------------------------
     # Algorithmic bytes: one 32-byte sector (holding the 16-byte neighbour
     # record) per walk transition.  Records larger than L2 are bound by HBM
@@ -357,6 +409,7 @@ def run_ours(args, wl, world, rank, local):
             "plain_queries_per_s": plain_qps, "plain_sample": plain_n,
             "batched_over_plain": (value / world) / plain_qps if plain_qps else None,
             "latency_ms": {"plain_p50": pct(50), "plain_p99": pct(99), "batch_step": total_ms / args.steps},
+            "server": server,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -384,6 +437,7 @@ def main():
     ap.add_argument("--cpu-probes", type=int, default=40, help="probes per sampled query in the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-server", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

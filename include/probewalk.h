@@ -170,6 +170,12 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
 pw_status pw_server_submit(pw_server* srv, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
                            uint64_t* ticket);
 pw_status pw_server_poll(pw_server* srv, uint64_t ticket, double* beta_hat);
+/* Move up to `cap` finished results out of the server (host arrays): ticket,
+ * estimate, per-query status and latency from submit to completion (ms, as
+ * seen by the scheduler thread); *count receives how many were written.  A
+ * collected ticket is no longer visible to pw_server_poll. */
+pw_status pw_server_collect(pw_server* srv, int64_t cap, uint64_t* tickets, double* beta_hat, int32_t* status,
+                            double* latency_ms, int64_t* count);
 /* Wait up to timeout_ms for every submitted ticket; PW_ERR_TIMEOUT otherwise. */
 pw_status pw_server_drain(pw_server* srv, int64_t timeout_ms);
 pw_status pw_server_destroy(pw_server* srv);

@@ -141,6 +141,8 @@ static pw_status upload(pw_graph* g, const int64_t* rp64, const int32_t* col) {
   PW_CUDA_TRY(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
   std::vector<int32_t> rp32((size_t)g->n + 1);
   for (int64_t i = 0; i <= g->n; ++i) rp32[(size_t)i] = (int32_t)rp64[i];
+  g->deg.resize((size_t)g->n);
+  for (int64_t i = 0; i < g->n; ++i) g->deg[(size_t)i] = rp32[(size_t)i + 1] - rp32[(size_t)i];
   int32_t *d_rp = nullptr, *d_col = nullptr;
   PW_CUDA_TRY(cudaMalloc(&d_rp, sizeof(int32_t) * (size_t)(g->n + 1)));
   PW_CUDA_TRY(cudaMalloc(&d_col, sizeof(int32_t) * (size_t)g->nnz));

@@ -79,6 +79,7 @@ struct pw_graph {
   int device = 0;
   int64_t n = 0, nnz = 0;
   int32_t d_min = 0, d_max = 0, bipartite = 0;
+  std::vector<int32_t> deg;  // host copy of the degrees (host-side query planning)
   int sm_count = 0;
   int last_walk_mode = 0;  // walk kernel chosen by the last batch (1 on-the-fly, 2 table)
   int4* d_rec = nullptr;   // nnz neighbour records

@@ -8,20 +8,14 @@
 #include <algorithm>
 #include <vector>
 
+#include "pw_budget.cuh"
 #include "pw_device.cuh"
 #include "pw_internal.h"
+#include "pw_walk.cuh"
 
 namespace pw {
 
 constexpr int kWalkThreads = 256;
-
-__host__ __device__ __forceinline__ double ceil_tol(double x) { return ceil(x * (1.0 - 1e-12)); }
-
-// R of Eq. R-value before the ceiling.
-__device__ __forceinline__ double r_theory_raw(double eps, int32_t L, double d_min, double ds, double dt) {
-  const double inv = 1.0 / ds + 1.0 / dt;
-  return 128.0 * (double)(L + 1) * (double)(L + 1) / (d_min * d_min * (1.0 - eps / 2.0) * inv * inv);
-}
 
 // ---------------------------------------------------------------------------
 // Budget of every query (Algorithm 1 line 1).  PILOT queries get their pilot
@@ -34,72 +28,14 @@ __global__ void budget_init_kernel(int64_t nq, const int64_t* __restrict__ qs, c
                                    QPlan* __restrict__ pilot) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
-  QPlan P;
-  memset(&P, 0, sizeof P);
   const int64_t s = qs[q], t = qt[q];
   const double eps = qeps[q];
   const int32_t L = qL[q];
-  P.eps = eps;
-  P.L = L;
-  P.status = PW_OK;
-  QPlan PP = P;
-  if (s < 0 || s >= n || t < 0 || t >= n || !(eps > 0.0 && eps < 1.0) || L < 0) {
-    P.status = PW_ERR_ARG;
-  } else {
-    P.s = (int32_t)s;
-    P.t = (int32_t)t;
-    P.seed = qseed ? qseed[q] : default_seed(A.global_seed, s, t, eps, L);
-    if (s != t) {
-      const double ds = (double)node[s].z, dt = (double)node[t].z, dmin = (double)A.d_min;
-      double B = 0.0, R = 0.0;
-      const double G = (double)A.G;
-      switch (A.mode) {
-        case PW_BUDGET_THEORY:
-          B = ceil_tol(448.0 / (eps * eps));
-          R = ceil_tol(r_theory_raw(eps, L, dmin, ds, dt));
-          if (R < 2.0) R = 2.0;
-          break;
-        case PW_BUDGET_SCALED:
-          B = ceil_tol(A.c_B * 448.0 / (eps * eps));
-          if (B < 1.0) B = 1.0;
-          R = ceil_tol(A.c_R * r_theory_raw(eps, L, dmin, ds, dt));
-          if (R < 2.0) R = 2.0;
-          if (R > (double)A.R_max) R = (double)A.R_max;
-          break;
-        case PW_BUDGET_FIXED:
-          B = (double)A.B_fixed;
-          R = (double)A.R_fixed;
-          break;
-        default:  // PILOT
-          B = ceil_tol(A.c_B / (eps * eps));
-          if (B < 1.0) B = 1.0;
-          R = 0.0;
-          break;
-      }
-      if (B * G >= 4294967296.0 || R >= 4294967296.0) {
-        P.status = PW_ERR_ARG;  // budget beyond 2^32 probes or replicas
-      } else {
-        P.B = (uint32_t)B;
-        P.G = A.G;
-        P.K = P.B * P.G;
-        P.R = (uint32_t)R;
-        P.chunks = (P.R + 31u) / 32u;
-        if (A.mode == PW_BUDGET_PILOT) {
-          PP.s = P.s;
-          PP.t = P.t;
-          PP.seed = P.seed;
-          PP.K = (uint32_t)A.K0;
-          PP.R = (uint32_t)A.R0;
-          PP.chunks = 1;
-        }
-      }
-    }
-  }
-  if (P.status != PW_OK) {
-    P.K = 0;
-    P.R = 0;
-    P.chunks = 0;
-  }
+  const bool ok = !(s < 0 || s >= n || t < 0 || t >= n || !(eps > 0.0 && eps < 1.0) || L < 0);
+  const uint64_t seed = !ok ? 0 : (qseed ? qseed[q] : default_seed(A.global_seed, s, t, eps, L));
+  const int32_t ds = ok ? node[s].z : 1, dt = ok ? node[t].z : 1;
+  QPlan P, PP;
+  plan_query(s, t, eps, L, seed, n, ds, dt, A, &P, &PP);
   plans[q] = P;
   if (pilot) pilot[q] = PP;
 }
@@ -113,35 +49,14 @@ __global__ void pilot_budget_kernel(int64_t nq, QPlan* __restrict__ plans, const
   const QPlan PP = pilot[q];
   if (PP.K == 0) return;
   QPlan& P = plans[q];
-  const double R0 = (double)PP.R;
   double sum_var = 0.0, sum_q = 0.0;
   for (uint32_t k = 0; k < PP.K; ++k) {
     const float* u = pilot_u + PP.u_begin + (uint64_t)k * PP.R;
     double S1 = 0.0, S2 = 0.0;
-    for (uint32_t p = 0; p < PP.R; ++p) {
-      const double x = (double)u[p];
-      S1 = __dadd_rn(S1, x);
-      S2 = __dadd_rn(S2, __dmul_rn(x, x));
-    }
-    const double Q = __ddiv_rn(__dsub_rn(__dmul_rn(S1, S1), S2), __dmul_rn(R0, __dsub_rn(R0, 1.0)));
-    sum_var = __dadd_rn(sum_var, __ddiv_rn(__dsub_rn(S2, __ddiv_rn(__dmul_rn(S1, S1), R0)), __dsub_rn(R0, 1.0)));
-    sum_q = __dadd_rn(sum_q, Q);
+    for (uint32_t p = 0; p < PP.R; ++p) accumulate_s(S1, S2, u[p]);
+    pilot_accumulate(sum_var, sum_q, S1, S2, PP.R);
   }
-  const double sigma2 = sum_var / (double)PP.K;
-  const double q_bar = sum_q / (double)PP.K;
-  const double ds = (double)node[P.s].z, dt = (double)node[P.t].z;
-  const double inv = 1.0 / ds + 1.0 / dt;
-  const double theta0 = (1.0 / 8.0) * (1.0 - P.eps / 2.0) * inv * inv;
-  const double theta = q_bar > theta0 ? q_bar : theta0;
-  double R = ceil_tol(A.c_R * 4.0 * sigma2 / theta);
-  if (R < 2.0) R = 2.0;
-  R = 32.0 * ceil(R / 32.0);
-  if (R > (double)A.R_max) R = (double)A.R_max;
-  P.R = (uint32_t)R;
-  P.chunks = (P.R + 31u) / 32u;
-  P.sigma2 = sigma2;
-  P.qbar = q_bar;
-  P.theta = theta;
+  pilot_finish(P, sum_var, sum_q, PP.K, node[P.s].z, node[P.t].z, A);
 }
 
 // Exclusive offsets of tiles (K*chunks), U slots (K*R) and probes (K); one
@@ -229,90 +144,6 @@ struct WalkArgs {
   uint32_t walk_tag, probe_tag;
 };
 
-// Probe entries evaluated on the fly (Section 3.3 generator): one cycle-walk
-// queue for the two walks so a lane pays iter(s) + iter(t) Feistel passes.
-struct ZOnTheFly {
-  const Probe& pr;
-  __device__ __forceinline__ void pair(uint32_t vs, uint32_t vt, int& zs, int& zt) const {
-    uint32_t pis, pit;
-    probe_pi_pair(pr, vs, vt, pis, pit);
-    zs = probe_z_from_pi(pr, pis);
-    zt = probe_z_from_pi(pr, pit);
-  }
-};
-
-// Probe entries read from the block's 2-bit table of z^(k) (built once per
-// probe): code bit 0 = nonzero, bit 1 = negative.
-struct ZTable {
-  const uint32_t* tab;
-  __device__ __forceinline__ static int decode(uint32_t c) { return (int)(c & 1u) - (int)(c & 2u); }
-  __device__ __forceinline__ void pair(uint32_t vs, uint32_t vt, int& zs, int& zt) const {
-    zs = decode(tab[vs >> 4] >> ((vs & 15u) << 1));
-    zt = decode(tab[vt >> 4] >> ((vt & 15u) << 1));
-  }
-};
-
-__device__ __forceinline__ uint32_t z_code(int z) { return z == 0 ? 0u : (z > 0 ? 1u : 3u); }
-
-// One replica: walks from s and t interleaved, a and b summed in FP32 in step
-// order (Eq. hatphi-def), U_p = a - b.  The load of X_{i+1} is issued before
-// the probe entry of X_i is evaluated so the gather latency overlaps the
-// integer work.
-template <bool DEBUG, class ZP>
-__device__ __forceinline__ float walk_pair(const int4* __restrict__ rec, const int4* __restrict__ node,
-                                           uint32_t* visits, uint32_t walk_tag, const ZP& zp, int32_t s,
-                                           int32_t t, int32_t L, uint64_t seed, uint64_t pair) {
-  int4 xs = __ldg(node + s), xt = __ldg(node + t);
-  int zs, zt;
-  zp.pair((uint32_t)xs.x, (uint32_t)xt.x, zs, zt);
-  float a = signed_term(zs, (uint32_t)xs.w);
-  float b = signed_term(zt, (uint32_t)xt.w);
-  if (DEBUG) {
-    atomicAdd(visits + xs.x, 1u);
-    atomicAdd(visits + xt.x, 1u);
-  }
-  if (L == 0) return __fsub_rn(a, b);
-  const uint64_t ws = 2 * pair, wt = ws + 1;
-  const PhiloxKeys keys = philox_keys(seed);
-  Philox4 rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), 0u, walk_tag, keys);
-  Philox4 rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), 0u, walk_tag, keys);
-  int4 ns = __ldg(rec + ((uint32_t)xs.y + __umulhi(rs.y, (uint32_t)xs.z)));
-  int4 nt = __ldg(rec + ((uint32_t)xt.y + __umulhi(rt.y, (uint32_t)xt.z)));
-  for (uint32_t blk = 0;; ++blk) {
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      if (w == 0 && blk == 0) continue;
-      const uint32_t i = blk * 4u + (uint32_t)w;  // ns, nt hold X_i
-      const bool more = i < (uint32_t)L;
-      int4 ns2 = ns, nt2 = nt;
-      if (more) {
-        uint32_t wsw, wtw;
-        if (w == 3) {
-          rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), blk + 1u, walk_tag, keys);
-          rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), blk + 1u, walk_tag, keys);
-          wsw = rs.x;
-          wtw = rt.x;
-        } else {
-          wsw = (w == 0) ? rs.y : (w == 1) ? rs.z : rs.w;
-          wtw = (w == 0) ? rt.y : (w == 1) ? rt.z : rt.w;
-        }
-        ns2 = __ldg(rec + ((uint32_t)ns.y + __umulhi(wsw, (uint32_t)ns.z)));
-        nt2 = __ldg(rec + ((uint32_t)nt.y + __umulhi(wtw, (uint32_t)nt.z)));
-      }
-      zp.pair((uint32_t)ns.x, (uint32_t)nt.x, zs, zt);
-      a = __fadd_rn(a, signed_term(zs, (uint32_t)ns.w));
-      b = __fadd_rn(b, signed_term(zt, (uint32_t)nt.w));
-      if (DEBUG) {
-        atomicAdd(visits + ns.x, 1u);
-        atomicAdd(visits + nt.x, 1u);
-      }
-      if (!more) return __fsub_rn(a, b);
-      ns = ns2;
-      nt = nt2;
-    }
-  }
-}
-
 // Persistent walk kernel: each warp pops tiles (query, probe k, 32 replicas)
 // from a device counter until the work runs out; lane l runs replica 32c + l.
 template <bool DEBUG>
@@ -355,7 +186,6 @@ __global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A,
   __shared__ uint32_t sh_tile;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t n = A.n;
-  const uint32_t nwords = (n + 15u) / 16u;
   const unsigned long long total = A.totals->probes;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -368,24 +198,7 @@ __global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A,
     const int64_t q = find_segment(probe_prefix, A.nq, j);
     const QPlan& P = A.plans[q];
     const uint32_t k = (uint32_t)(j - P.probe_begin);
-    {
-      const Probe pr = make_probe(n, P.seed, k, A.probe_tag);
-      uint32_t w = threadIdx.x, v = w * 16u, x = v, acc = 0;
-      while (w < nwords) {
-        x = feistel_once(pr, x);
-        if (x < n) {
-          acc |= z_code(probe_z_from_pi(pr, x)) << ((v & 15u) << 1);
-          ++v;
-          if ((v & 15u) == 0 || v >= n) {
-            tab[w] = acc;
-            acc = 0;
-            w += blockDim.x;
-            v = w * 16u;
-          }
-          x = v;
-        }
-      }
-    }
+    build_probe_table(make_probe(n, P.seed, k, A.probe_tag), tab, n);
     __syncthreads();
     const ZTable zp{tab};
     const uint32_t R = P.R, chunks = P.chunks;
@@ -418,13 +231,8 @@ __global__ void probe_finish_kernel(const QPlan* __restrict__ plans, int64_t nq,
     const unsigned long long k = j - P.probe_begin;
     const float* x = u + P.u_begin + k * P.R;
     double S1 = 0.0, S2 = 0.0;
-    for (uint32_t p = 0; p < P.R; ++p) {
-      const double v = (double)x[p];
-      S1 = __dadd_rn(S1, v);
-      S2 = __dadd_rn(S2, __dmul_rn(v, v));
-    }
-    const double Rd = (double)P.R;
-    qbuf[j] = __ddiv_rn(__dsub_rn(__dmul_rn(S1, S1), S2), __dmul_rn(Rd, __dsub_rn(Rd, 1.0)));
+    for (uint32_t p = 0; p < P.R; ++p) accumulate_s(S1, S2, x[p]);
+    qbuf[j] = u_statistic(S1, S2, P.R);
   }
 }
 

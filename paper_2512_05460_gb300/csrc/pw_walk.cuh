@@ -1,0 +1,118 @@
+// Walk building blocks shared by the batch kernels and the server kernel:
+// the two ways of reading probe entries (evaluated per visit, or from a
+// per-probe shared-memory table) and one replica of Algorithm 1's inner loop.
+#pragma once
+#include <stdint.h>
+
+#include "pw_device.cuh"
+
+namespace pw {
+
+// Probe entries evaluated on the fly (Section 3.3 generator): one cycle-walk
+// queue for the two walks so a lane pays iter(s) + iter(t) Feistel passes.
+struct ZOnTheFly {
+  const Probe& pr;
+  __device__ __forceinline__ void pair(uint32_t vs, uint32_t vt, int& zs, int& zt) const {
+    uint32_t pis, pit;
+    probe_pi_pair(pr, vs, vt, pis, pit);
+    zs = probe_z_from_pi(pr, pis);
+    zt = probe_z_from_pi(pr, pit);
+  }
+};
+
+// Probe entries read from the block's 2-bit table of z^(k) (built once per
+// probe): code bit 0 = nonzero, bit 1 = negative.
+struct ZTable {
+  const uint32_t* tab;
+  __device__ __forceinline__ static int decode(uint32_t c) { return (int)(c & 1u) - (int)(c & 2u); }
+  __device__ __forceinline__ void pair(uint32_t vs, uint32_t vt, int& zs, int& zt) const {
+    zs = decode(tab[vs >> 4] >> ((vs & 15u) << 1));
+    zt = decode(tab[vt >> 4] >> ((vt & 15u) << 1));
+  }
+};
+
+__device__ __forceinline__ uint32_t z_code(int z) { return z == 0 ? 0u : (z > 0 ? 1u : 3u); }
+
+// One replica: walks from s and t interleaved, a and b summed in FP32 in step
+// order (Eq. hatphi-def), U_p = a - b.  The load of X_{i+1} is issued before
+// the probe entry of X_i is evaluated so the gather latency overlaps the
+// integer work.
+template <bool DEBUG, class ZP>
+__device__ __forceinline__ float walk_pair(const int4* __restrict__ rec, const int4* __restrict__ node,
+                                           uint32_t* visits, uint32_t walk_tag, const ZP& zp, int32_t s,
+                                           int32_t t, int32_t L, uint64_t seed, uint64_t pair) {
+  int4 xs = __ldg(node + s), xt = __ldg(node + t);
+  int zs, zt;
+  zp.pair((uint32_t)xs.x, (uint32_t)xt.x, zs, zt);
+  float a = signed_term(zs, (uint32_t)xs.w);
+  float b = signed_term(zt, (uint32_t)xt.w);
+  if (DEBUG) {
+    atomicAdd(visits + xs.x, 1u);
+    atomicAdd(visits + xt.x, 1u);
+  }
+  if (L == 0) return __fsub_rn(a, b);
+  const uint64_t ws = 2 * pair, wt = ws + 1;
+  const PhiloxKeys keys = philox_keys(seed);
+  Philox4 rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), 0u, walk_tag, keys);
+  Philox4 rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), 0u, walk_tag, keys);
+  int4 ns = __ldg(rec + ((uint32_t)xs.y + __umulhi(rs.y, (uint32_t)xs.z)));
+  int4 nt = __ldg(rec + ((uint32_t)xt.y + __umulhi(rt.y, (uint32_t)xt.z)));
+  for (uint32_t blk = 0;; ++blk) {
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      if (w == 0 && blk == 0) continue;
+      const uint32_t i = blk * 4u + (uint32_t)w;  // ns, nt hold X_i
+      const bool more = i < (uint32_t)L;
+      int4 ns2 = ns, nt2 = nt;
+      if (more) {
+        uint32_t wsw, wtw;
+        if (w == 3) {
+          rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), blk + 1u, walk_tag, keys);
+          rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), blk + 1u, walk_tag, keys);
+          wsw = rs.x;
+          wtw = rt.x;
+        } else {
+          wsw = (w == 0) ? rs.y : (w == 1) ? rs.z : rs.w;
+          wtw = (w == 0) ? rt.y : (w == 1) ? rt.z : rt.w;
+        }
+        ns2 = __ldg(rec + ((uint32_t)ns.y + __umulhi(wsw, (uint32_t)ns.z)));
+        nt2 = __ldg(rec + ((uint32_t)nt.y + __umulhi(wtw, (uint32_t)nt.z)));
+      }
+      zp.pair((uint32_t)ns.x, (uint32_t)nt.x, zs, zt);
+      a = __fadd_rn(a, signed_term(zs, (uint32_t)ns.w));
+      b = __fadd_rn(b, signed_term(zt, (uint32_t)nt.w));
+      if (DEBUG) {
+        atomicAdd(visits + ns.x, 1u);
+        atomicAdd(visits + nt.x, 1u);
+      }
+      if (!more) return __fsub_rn(a, b);
+      ns = ns2;
+      nt = nt2;
+    }
+  }
+}
+
+// z^(k) of every node into a 2-bit shared-memory table (16 nodes per word),
+// one Feistel cycle-walk per node.  Each thread owns whole words and runs a
+// flat queue (one Feistel pass per iteration, moving to its next node when a
+// pass lands in [n]), so lanes stay busy even though cycle-walk lengths vary.
+__device__ __forceinline__ void build_probe_table(const Probe& pr, uint32_t* tab, uint32_t n) {
+  const uint32_t nwords = (n + 15u) / 16u;
+  uint32_t w = threadIdx.x, v = w * 16u, x = v, acc = 0;
+  while (w < nwords) {
+    x = feistel_once(pr, x);
+    if (x < n) {
+      acc |= z_code(probe_z_from_pi(pr, x)) << ((v & 15u) << 1);
+      ++v;
+      if ((v & 15u) == 0 || v >= n) {
+        tab[w] = acc;
+        acc = 0;
+        w += blockDim.x;
+        v = w * 16u;
+      }
+      x = v;
+    }
+  }
+}
+
+}  // namespace pw

@@ -97,6 +97,7 @@ SIGNATURES = {
     "pw_server_create": (_i32, [_vp, P(pw_params), ctypes.c_size_t, P(_vp)]),
     "pw_server_submit": (_i32, [_vp, _i64, _i64, _dbl, _i32, P(_u64), P(_u64)]),
     "pw_server_poll": (_i32, [_vp, _u64, P(_dbl)]),
+    "pw_server_collect": (_i32, [_vp, _i64, P(_u64), P(_dbl), P(_i32), P(_dbl), P(_i64)]),
     "pw_server_drain": (_i32, [_vp, _i64]),
     "pw_server_destroy": (_i32, [_vp]),
     "pw_debug_philox": (_i32, [_vp, P(_u32), P(_u32), P(_u32)]),
@@ -273,6 +274,18 @@ def pw_server_poll(srv: int, ticket: int):
     out = _dbl()
     st = _check(lib().pw_server_poll(srv, ticket, ctypes.byref(out)))
     return st, out.value
+
+
+def pw_server_collect(srv: int, cap: int = 65536):
+    """Finished results: (tickets, beta_hat, status, latency_ms) numpy arrays."""
+    tk = np.zeros(cap, np.uint64)
+    b = np.zeros(cap, np.float64)
+    st = np.zeros(cap, np.int32)
+    lat = np.zeros(cap, np.float64)
+    n = _i64()
+    _check(lib().pw_server_collect(srv, cap, _p(tk, _u64), _p(b, _dbl), _p(st, _i32), _p(lat, _dbl), ctypes.byref(n)))
+    k = n.value
+    return tk[:k], b[:k], st[:k], lat[:k]
 
 
 def pw_server_drain(srv: int, timeout_ms: int = 60000) -> None:

@@ -1,0 +1,157 @@
+"""Continuous-batching server (persistent kernel + device work queue): every
+estimate equals the batch entry point's (hence the oracle's) bit for bit,
+whether a query runs alone, in a burst, or arrives while others are on the GPU;
+admission by accumulator memory; invalid queries; shutdown with work queued."""
+
+import time
+
+import numpy as np
+import pytest
+
+from pw_inputs import barabasi_albert, eps_uniform, query_seeds, uniform_pairs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pw():
+    from paper_2512_05460_gb300 import build
+
+    build.build()
+    from paper_2512_05460_gb300 import probewalk
+
+    probewalk.lib()
+    return probewalk
+
+
+@pytest.fixture(scope="module")
+def tiny(pw, tiny_graph):
+    g = pw.Graph(tiny_graph.row_ptr, tiny_graph.col_idx)
+    yield tiny_graph, g
+    g.close()
+
+
+def _queries(n, count, seed):
+    s, t = uniform_pairs(n, count, seed)
+    eps = eps_uniform(count, 0.15, 0.35, seed + 1)
+    L = np.random.default_rng(seed + 2).integers(0, 40, size=count).astype(np.int32)
+    seeds = query_seeds(count, seed + 3)
+    return s, t, eps, L, seeds
+
+
+def _serve(pw, g, s, t, eps, L, seeds, params=None, accum=1 << 26, gap_s=0.0, timeout_ms=120000):
+    srv = pw.pw_server_create(g.handle, params, accum)
+    try:
+        tickets = []
+        for i in range(s.size):
+            tickets.append(pw.pw_server_submit(srv, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i])))
+            if gap_s:
+                time.sleep(gap_s)
+        pw.pw_server_drain(srv, timeout_ms)
+        out = np.empty(s.size)
+        for i, tk in enumerate(tickets):
+            st, b = pw.pw_server_poll(srv, tk)
+            assert st == pw.PW_OK
+            out[i] = b
+        return out
+    finally:
+        pw.pw_server_destroy(srv)
+
+
+def test_server_burst_equals_batch(pw, tiny):
+    host, g = tiny
+    q = _queries(host.n, 48, 500)
+    want, st = pw.pw_query_batch(g.handle, *q)
+    assert np.all(st == 0)
+    np.testing.assert_array_equal(_serve(pw, g, *q), want)
+
+
+def test_server_arrivals_while_busy_equal_batch(pw, tiny):
+    host, g = tiny
+    q = _queries(host.n, 40, 600)
+    want, _ = pw.pw_query_batch(g.handle, *q)
+    np.testing.assert_array_equal(_serve(pw, g, *q, gap_s=0.002), want)
+
+
+def test_server_alone_equals_mix(pw, tiny):
+    host, g = tiny
+    s, t, eps, L, seeds = _queries(host.n, 12, 700)
+    mixed = _serve(pw, g, s, t, eps, L, seeds)
+    srv = pw.pw_server_create(g.handle, None, 1 << 24)
+    try:
+        for i in range(12):  # one query in flight at a time
+            tk = pw.pw_server_submit(srv, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i]))
+            pw.pw_server_drain(srv, 60000)
+            st, b = pw.pw_server_poll(srv, tk)
+            assert st == pw.PW_OK and b == mixed[i]
+    finally:
+        pw.pw_server_destroy(srv)
+
+
+def test_server_admission_by_memory(pw, tiny):
+    """A 1 MiB accumulator pool holds only a few queries at a time; the rest
+    wait in the host queue and are admitted as memory frees up."""
+    host, g = tiny
+    q = _queries(host.n, 64, 800)
+    want, _ = pw.pw_query_batch(g.handle, *q)
+    np.testing.assert_array_equal(_serve(pw, g, *q, accum=1 << 20), want)
+
+
+def test_server_fixed_budget(pw, tiny):
+    host, g = tiny
+    q = _queries(host.n, 20, 900)
+    params = pw.make_params(budget_mode=pw.PW_BUDGET_FIXED, B=5, G=7, R=45)
+    want, _ = pw.pw_query_batch(g.handle, *q, params)
+    np.testing.assert_array_equal(_serve(pw, g, *q, params=params), want)
+
+
+def test_server_invalid_and_same_node(pw, tiny):
+    host, g = tiny
+    srv = pw.pw_server_create(g.handle, None, 1 << 24)
+    try:
+        t_same = pw.pw_server_submit(srv, 3, 3, 0.2, 20, 1)
+        t_bad = pw.pw_server_submit(srv, 3, 999, 0.2, 20, 1)
+        t_ok = pw.pw_server_submit(srv, 3, 4, 0.2, 20, 1)
+        pw.pw_server_drain(srv, 60000)
+        assert pw.pw_server_poll(srv, t_same) == (pw.PW_OK, 0.0)
+        with pytest.raises(pw.PWError) as e:
+            pw.pw_server_poll(srv, t_bad)
+        assert e.value.status == pw.PW_ERR_ARG
+        st, b = pw.pw_server_poll(srv, t_ok)
+        assert st == pw.PW_OK and b == pw.pw_query(g.handle, 3, 4, 0.2, 20, 1)
+        with pytest.raises(pw.PWError):
+            pw.pw_server_poll(srv, 10**9)  # unknown ticket
+    finally:
+        pw.pw_server_destroy(srv)
+
+
+def test_server_collect_and_destroy_with_queue(pw, tiny):
+    host, g = tiny
+    s, t, eps, L, seeds = _queries(host.n, 30, 1000)
+    srv = pw.pw_server_create(g.handle, None, 1 << 20)
+    for i in range(30):
+        pw.pw_server_submit(srv, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i]))
+    time.sleep(0.01)
+    tk, b, st, lat = pw.pw_server_collect(srv)
+    assert np.all(lat >= 0)
+    pw.pw_server_destroy(srv)  # queued work is cancelled, in-flight work finishes; no hang
+
+
+def test_server_ba_equals_batch(pw):
+    host = barabasi_albert(100_000, 5, 1)
+    with pw.Graph(host.row_ptr, host.col_idx) as g:
+        s, t = uniform_pairs(host.n, 16, 1100)
+        seeds = query_seeds(16, 1101)
+        want, st = pw.pw_query_batch(g.handle, s, t, 0.2, 100, seeds)
+        assert np.all(st == 0)
+        got = _serve(pw, g, s, t, np.full(16, 0.2), np.full(16, 100, np.int32), seeds, accum=1 << 28)
+        np.testing.assert_array_equal(got, want)
+
+
+def test_server_idle_exit_and_relaunch(pw, tiny):
+    """Gaps longer than the kernel's idle window (5 ms): the grid exits between
+    queries and is relaunched by the scheduler; estimates are unchanged."""
+    host, g = tiny
+    q = _queries(host.n, 6, 1200)
+    want, _ = pw.pw_query_batch(g.handle, *q)
+    np.testing.assert_array_equal(_serve(pw, g, *q, gap_s=0.02), want)
