@@ -160,6 +160,20 @@ pw_status pw_query_batch_noalloc(pw_graph* g, int64_t count, const int64_t* d_s,
                                  const double* d_eps, const int32_t* d_L, const uint64_t* d_seeds,
                                  const pw_params* params, double* d_beta_hat, int32_t* d_status, void* stream);
 
+/* ---- sharded query (one query split across GPUs) ---------------------------
+ * pw_query_blocks: the median-of-means blocks [g_begin, g_end) of one query
+ * (Eq. final-estimator before the median): the same budget and the same
+ * walks (probe indices keep their values) as the whole query, restricted to
+ * probes g_begin*B .. g_end*B - 1.  block_means (host, g_end - g_begin) gets
+ * the block means.  0 <= g_begin < g_end <= G; s != t.  Ranks that own
+ * disjoint block ranges gather their means and pw_block_median gives the
+ * estimate of the unsharded query, bit for bit. */
+pw_status pw_query_blocks(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
+                          const pw_params* params, int64_t g_begin, int64_t g_end, double* block_means);
+/* pw_block_median: median of G block means (host arrays; mean of the two
+ * middle values for even G), the last step of Eq. final-estimator. */
+pw_status pw_block_median(const double* block_means, int64_t G, double* out);
+
 /* ---- server (continuous batching) ----------------------------------------
  * A server keeps the graph and the per-query accumulators on the device and
  * runs a persistent kernel fed by a device work queue.  Queries are admitted

@@ -134,6 +134,22 @@ uint64_t pw_launch_count(int reset) {
 
 const char* pw_version(void) { return "probewalk-gb300 0.1 (sm_103a)"; }
 
+pw_status pw_block_median(const double* block_means, int64_t G, double* out) {
+  if (!block_means || !out || G < 1) return pw::set_error(PW_ERR_ARG, "NULL argument or G < 1");
+  std::vector<double> m(block_means, block_means + G);
+  for (int64_t i = 1; i < G; ++i) {  // insertion sort, as the device median
+    const double v = m[(size_t)i];
+    int64_t j = i;
+    while (j > 0 && m[(size_t)j - 1] > v) {
+      m[(size_t)j] = m[(size_t)j - 1];
+      --j;
+    }
+    m[(size_t)j] = v;
+  }
+  *out = (G & 1) ? m[(size_t)(G / 2)] : (m[(size_t)(G / 2 - 1)] + m[(size_t)(G / 2)]) / 2.0;
+  return PW_OK;
+}
+
 uint64_t pw_default_seed(uint64_t global_seed, int64_t s, int64_t t, double eps, int32_t L) {
   return pw::default_seed(global_seed, s, t, eps, L);
 }

@@ -23,7 +23,7 @@ struct QPlan {
   int32_t status;        // pw_status of this query
   uint32_t K, R, B, G;
   uint32_t chunks;       // ceil(R / 32)
-  uint32_t pad0;
+  uint32_t k_begin;      // first probe index (a range of blocks of a sharded query; else 0)
   double eps;
   double sigma2, qbar, theta;  // pilot diagnostics
 };
@@ -109,6 +109,9 @@ pw_status resolve_budget(const pw_params* params, const pw_graph* g, BudgetArgs*
 struct DebugOut {
   uint32_t* visits = nullptr;  // device, n counters of visits by the main walks
   bool budget_only = false;    // stop after the budget (and pilot) stage
+  int64_t g_begin = -1;        // >= 0: run only median-of-means blocks [g_begin, g_end) of query 0
+  int64_t g_end = -1;
+  double* block_means = nullptr;  // device, g_end - g_begin block means (instead of the median)
 };
 pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t, const double* d_eps,
                     const int32_t* d_L, const uint64_t* d_seeds, const pw_params* params, double* d_beta,

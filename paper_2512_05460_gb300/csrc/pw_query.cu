@@ -159,15 +159,16 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkArgs A) {
     const QPlan& P = A.plans[q];
     const uint32_t chunks = P.chunks, R = P.R;
     const unsigned long long local = tile - P.tile_begin;
-    const uint32_t k = (uint32_t)(local / chunks);
-    const uint32_t c = (uint32_t)(local - (unsigned long long)k * chunks);
+    const uint32_t kl = (uint32_t)(local / chunks);
+    const uint32_t c = (uint32_t)(local - (unsigned long long)kl * chunks);
     const uint32_t p = c * 32u + lane;
     if (p >= R) continue;
+    const uint32_t k = P.k_begin + kl;
     const Probe pr = make_probe(A.n, P.seed, k, A.probe_tag);
     const uint64_t pair = (uint64_t)k * R + p;
     const ZOnTheFly zp{pr};
     const float U = walk_pair<DEBUG>(A.rec, A.node, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
-    A.u[P.u_begin + pair] = U;
+    A.u[P.u_begin + (uint64_t)kl * R + p] = U;
   }
 }
 
@@ -197,7 +198,8 @@ __global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A,
     if (j >= total) return;
     const int64_t q = find_segment(probe_prefix, A.nq, j);
     const QPlan& P = A.plans[q];
-    const uint32_t k = (uint32_t)(j - P.probe_begin);
+    const uint32_t kl = (uint32_t)(j - P.probe_begin);
+    const uint32_t k = P.k_begin + kl;
     build_probe_table(make_probe(n, P.seed, k, A.probe_tag), tab, n);
     __syncthreads();
     const ZTable zp{tab};
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A,
       if (p < R) {
         const uint64_t pair = (uint64_t)k * R + p;
         const float U = walk_pair<DEBUG>(A.rec, A.node, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
-        A.u[P.u_begin + pair] = U;
+        A.u[P.u_begin + (uint64_t)kl * R + p] = U;
       }
     }
     __syncthreads();
@@ -271,6 +273,30 @@ __global__ void mom_kernel(const QPlan* __restrict__ plans, const double* __rest
     beta[q] = med;
     status[q] = PW_OK;
   }
+}
+
+// Sharded query: keep only median-of-means blocks [g0, g1) of query 0; probe
+// indices keep their global values (k_begin), so the walks are those of the
+// whole query.
+__global__ void restrict_blocks_kernel(QPlan* plans, uint32_t g0, uint32_t g1) {
+  QPlan& P = plans[0];
+  if (P.status != PW_OK || P.K == 0) return;
+  P.k_begin = g0 * P.B;
+  P.K = (g1 - g0) * P.B;
+  P.G = g1 - g0;
+}
+
+// Block means of a sharded query (Eq. final-estimator before the median).
+__global__ void block_means_kernel(const QPlan* __restrict__ plans, const double* __restrict__ qbuf,
+                                   double* __restrict__ means, int32_t* __restrict__ status) {
+  const QPlan& P = plans[0];
+  for (uint32_t g = threadIdx.x; g < P.G; g += blockDim.x) {
+    const double* x = qbuf + P.probe_begin + (uint64_t)g * P.B;
+    double sum = 0.0;
+    for (uint32_t k = 0; k < P.B; ++k) sum = __dadd_rn(sum, x[k]);
+    means[g] = __ddiv_rn(sum, (double)P.B);
+  }
+  if (threadIdx.x == 0) status[0] = P.status;
 }
 
 static int walk_grid(pw_graph* g, bool debug) {
@@ -411,6 +437,12 @@ pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_
     count_launch();
     PW_CUDA_TRY(cudaGetLastError());
   }
+  const bool sharded = dbg && dbg->g_begin >= 0;
+  if (sharded) {
+    restrict_blocks_kernel<<<1, 1, 0, stream>>>(plans, (uint32_t)dbg->g_begin, (uint32_t)dbg->g_end);
+    count_launch();
+    PW_CUDA_TRY(cudaGetLastError());
+  }
   scan_kernel<<<1, 1024, 0, stream>>>(plans, count, prefix, totals);
   count_launch();
   PW_CUDA_TRY(cudaGetLastError());
@@ -468,7 +500,10 @@ pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_
     count_launch();
     PW_CUDA_TRY(cudaGetLastError());
   }
-  mom_kernel<<<(unsigned)count, 128, 0, stream>>>(plans, (const double*)ws.q.ptr, d_beta, d_status);
+  if (sharded)
+    block_means_kernel<<<1, 128, 0, stream>>>(plans, (const double*)ws.q.ptr, dbg->block_means, d_status);
+  else
+    mom_kernel<<<(unsigned)count, 128, 0, stream>>>(plans, (const double*)ws.q.ptr, d_beta, d_status);
   count_launch();
   PW_CUDA_TRY(cudaGetLastError());
   prof_end(g, stream, ev_fin, 2);
@@ -656,6 +691,37 @@ pw_status pw_debug_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t 
     }
   }
   free_buffer(vis);
+  return st;
+}
+
+pw_status pw_query_blocks(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
+                          const pw_params* params, int64_t g_begin, int64_t g_end, double* block_means) {
+  if (!g || !block_means) return set_error(PW_ERR_ARG, "NULL argument");
+  if (s < 0 || s >= g->n || t < 0 || t >= g->n || s == t) return set_error(PW_ERR_ARG, "need 0 <= s != t < n");
+  if (!(eps > 0.0 && eps < 1.0) || L < 0) return set_error(PW_ERR_ARG, "eps must lie in (0, 1) and L >= 0");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  BudgetArgs ba;
+  pw_status st = resolve_budget(params, g, &ba, nullptr);
+  if (st != PW_OK) return st;
+  if (g_begin < 0 || g_end <= g_begin || g_end > (int64_t)ba.G) return set_error(PW_ERR_ARG, "block range outside [0, G)");
+  const uint64_t sd = seed ? *seed : default_seed(ba.global_seed, s, t, eps, L);
+  DebugOut dbg;
+  DeviceBuffer means;
+  if ((st = ensure_buffer(means, sizeof(double) * (size_t)(g_end - g_begin))) != PW_OK) return st;
+  dbg.g_begin = g_begin;
+  dbg.g_end = g_end;
+  dbg.block_means = (double*)means.ptr;
+  double beta;
+  int32_t qst = 0;
+  st = host_batch(g, 1, &s, &t, &eps, &L, &sd, params, &beta, &qst, &dbg);
+  if (st == PW_OK && qst != PW_OK) st = set_error((pw_status)qst, "query rejected");
+  if (st == PW_OK) {
+    cudaError_t e = cudaMemcpy(block_means, means.ptr, sizeof(double) * (size_t)(g_end - g_begin),
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = cuda_error(e, "block means copy-out");
+  }
+  free_buffer(means);
   return st;
 }
 

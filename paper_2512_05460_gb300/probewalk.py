@@ -94,6 +94,8 @@ SIGNATURES = {
                               P(_i32)]),
     "pw_query_batch_device": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, P(pw_params), _vp, _vp, _vp]),
     "pw_query_batch_noalloc": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, P(pw_params), _vp, _vp, _vp]),
+    "pw_query_blocks": (_i32, [_vp, _i64, _i64, _dbl, _i32, P(_u64), P(pw_params), _i64, _i64, P(_dbl)]),
+    "pw_block_median": (_i32, [P(_dbl), _i64, P(_dbl)]),
     "pw_server_create": (_i32, [_vp, P(pw_params), ctypes.c_size_t, P(_vp)]),
     "pw_server_submit": (_i32, [_vp, _i64, _i64, _dbl, _i32, P(_u64), P(_u64)]),
     "pw_server_poll": (_i32, [_vp, _u64, P(_dbl)]),
@@ -253,6 +255,21 @@ def pw_query_batch_noalloc(g: int, count: int, d_s, d_t, d_eps, d_L, d_seeds, d_
     _check(lib().pw_query_batch_noalloc(g, count, _dev_ptr(d_s), _dev_ptr(d_t), _dev_ptr(d_eps), _dev_ptr(d_L),
                                         _dev_ptr(d_seeds), _params(params), _dev_ptr(d_beta), _dev_ptr(d_status),
                                         stream))
+
+
+def pw_query_blocks(g: int, s: int, t: int, eps: float, L: int, g_begin: int, g_end: int, seed=None,
+                    params=None) -> np.ndarray:
+    out = np.zeros(g_end - g_begin, np.float64)
+    _check(lib().pw_query_blocks(g, s, t, eps, L, _seed_ptr(seed), _params(params), g_begin, g_end,
+                                 _p(out, _dbl)))
+    return out
+
+
+def pw_block_median(block_means) -> float:
+    m = _arr(block_means, np.float64)
+    out = _dbl()
+    _check(lib().pw_block_median(_p(m, _dbl), m.size, ctypes.byref(out)))
+    return out.value
 
 
 # ---- server ----------------------------------------------------------------

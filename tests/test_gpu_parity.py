@@ -302,3 +302,13 @@ def test_ba_full_size_accuracy_vs_series(ba_batch):
     want = exact.series_beta_many(host.row_ptr, host.col_idx, host.n, b["s"][idx], b["t"][idx], 200)
     rel = np.abs(b["beta"][idx] - want) / want
     assert (rel <= 0.1).mean() >= 0.95
+
+
+def test_sharded_blocks_equal_whole_query(pw, tiny):
+    """pw_query_blocks over disjoint block ranges + pw_block_median == pw_query."""
+    host, g = tiny
+    for s, t, seed in ((3, 77, 12345), (10, 190, 7)):
+        whole = pw.pw_query(g.handle, s, t, 0.2, 32, seed)
+        G = pw.pw_budget(g.handle, s, t, 0.2, 32, seed)["G"]
+        parts = [pw.pw_query_blocks(g.handle, s, t, 0.2, 32, a, b, seed) for a, b in ((0, 13), (13, 30), (30, G))]
+        assert pw.pw_block_median(np.concatenate(parts)) == whole
