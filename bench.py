@@ -36,7 +36,22 @@ WORKLOADS = {
                    eps=0.1, pair_seed=101, seed_seed=1001),
     "tiny-er200": dict(graph="tiny-er200", desc="Erdos-Renyi G(200, 8/199) + cycle (seed 0)", queries=64, L=32,
                        eps=0.2, pair_seed=100, seed_seed=200),
+    "rmat-20": dict(graph="rmat-20", desc="R-MAT 2^20 ef16 (.57,.19,.19,.05) symmetrised, LCC (seed 2)",
+                    queries=1000, L=500, eps=("uniform", 0.05, 0.2), pair_seed=102, seed_seed=1002),
+    "grid-2000": dict(graph="grid-2000", desc="2000x2000 grid, 5% edges deleted, LCC (seed 3), bipartite",
+                      queries=1000, L=2000, eps=("choice", 0.05, 0.1, 0.2), pair_seed=103, seed_seed=1003),
 }
+
+
+def workload_eps(wl: dict, count: int, rank: int = 0) -> np.ndarray:
+    from pw_inputs import eps_choice, eps_uniform
+
+    e = wl["eps"]
+    if isinstance(e, float):
+        return np.full(count, e)
+    if e[0] == "uniform":
+        return eps_uniform(count, e[1], e[2], wl["pair_seed"] + 7919 * rank)
+    return eps_choice(count, list(e[1:]), wl["pair_seed"] + 7919 * rank)
 
 SECTOR_BYTES = 32  # one 16-byte neighbour record per transition lives in one 32-byte sector
 L2_BYTES = 129 << 20
@@ -166,8 +181,10 @@ def cpu_oracle_sample(host, s, t, seeds, wl, n_queries: int, probes_per_query: i
     oracle.build()
     idx = [(offset + i) % s.size for i in range(n_queries)]
 
+    eps_all = workload_eps(wl, s.size)
+
     def one(i):
-        b = oracle.budget(host, int(s[i]), int(t[i]), wl["eps"], wl["L"], int(seeds[i]))
+        b = oracle.budget(host, int(s[i]), int(t[i]), float(eps_all[i]), wl["L"], int(seeds[i]))
         P = min(probes_per_query, b["K"])
         oracle.probe_q(host, int(s[i]), int(t[i]), wl["L"], int(seeds[i]), b["R"], np.arange(P))
         pilot = 2 * 64 * 32 * wl["L"]
@@ -271,7 +288,7 @@ def run_ours(args, wl, world, rank, local):
     if args.queries:
         s, t, seeds = s[:args.queries], t[:args.queries], seeds[:args.queries]
     nq = s.size
-    eps = np.full(nq, wl["eps"])
+    eps = workload_eps(wl, nq, rank)
     L = np.full(nq, wl["L"], np.int32)
     g = pw.Graph(host.row_ptr, host.col_idx, device=local)
     params = pw.make_params(c_B=args.c_B, walk_mode=args.walk_mode)

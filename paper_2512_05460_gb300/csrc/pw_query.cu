@@ -173,13 +173,13 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkArgs A) {
 }
 
 // Probe-major kernel: a block claims one probe k of one query, writes the
-// whole vector z^(k) into a 2-bit shared-memory table (one Feistel cycle-walk
-// per node, a flat per-lane queue so lanes stay busy), then its warps run the
+// whole vector z^(k) into a shared-memory table (sign bits plus the zero set;
+// one Feistel cycle-walk per node), then its warps run the
 // probe's 32-replica tiles reading z from the table.  Same values as the
 // on-the-fly kernel; cheaper whenever a probe's walks visit more nodes than
 // the graph has (2 R (L+1) > n).
 template <bool DEBUG>
-__global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A,
+__global__ void __launch_bounds__(kWalkThreads, 4) walk_table_kernel(WalkArgs A,
                                                                   const unsigned long long* __restrict__ probe_prefix,
                                                                   unsigned long long* __restrict__ probe_counter) {
   extern __shared__ uint32_t tab[];
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A,
     const uint32_t k = P.k_begin + kl;
     build_probe_table(make_probe(n, P.seed, k, A.probe_tag), tab, n);
     __syncthreads();
-    const ZTable zp{tab};
+    const ZTable zp = table_reader(tab, n);
     const uint32_t R = P.R, chunks = P.chunks;
     for (;;) {
       uint32_t c = 0;
@@ -339,8 +339,8 @@ static void prof_end(pw_graph* g, cudaStream_t stream, cudaEvent_t a, int kind) 
   g->prof.spans.push_back({a, b, kind});
 }
 
-// Largest graph whose 2-bit probe table fits in shared memory next to the kernel's own state.
-static size_t table_bytes(const pw_graph* g) { return sizeof(uint32_t) * (size_t)((g->n + 15) / 16); }
+// Largest graph whose probe table (1 bit per node) fits in shared memory next to the kernel's own state.
+static size_t table_bytes(const pw_graph* g) { return sizeof(uint32_t) * (size_t)table_words((uint32_t)g->n); }
 static constexpr size_t kMaxTableBytes = 200 * 1024;
 
 static int table_grid(pw_graph* g, bool debug, size_t smem) {

@@ -137,7 +137,7 @@ __device__ bool find_job(const ServerArgs& A, uint32_t& slot, uint32_t& stage, u
   return false;
 }
 
-__global__ void __launch_bounds__(kServerThreads, 4) server_kernel(ServerArgs A) {
+__global__ void __launch_bounds__(kServerThreads, 5) server_kernel(ServerArgs A) {
   extern __shared__ uint32_t smem[];
   uint32_t* tab = smem;
   float* su = (float*)(smem + A.table_words);
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kServerThreads, 4) server_kernel(ServerArgs A)
         const uint64_t pair = (uint64_t)k * R + p;
         float U;
         if (table) {
-          const ZTable zp{tab};
+          const ZTable zp = table_reader(tab, A.n);
           U = walk_pair<false>(A.rec, A.node, nullptr, walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
         } else {
           const ZOnTheFly zp{pr};
@@ -556,7 +556,7 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
   // shared memory: probe table (if it fits next to the U_p buffer) + U_p
   const size_t ubytes = sizeof(float) * kServerRmax;
   // rounded to 16 bytes so the U_p area that follows (reused for FP64 block means) stays aligned
-  const size_t tbytes = (sizeof(uint32_t) * (size_t)((g->n + 15) / 16) + 15) & ~(size_t)15;
+  const size_t tbytes = (sizeof(uint32_t) * (size_t)table_words((uint32_t)g->n) + 15) & ~(size_t)15;
   sv->smem = ubytes + ((tbytes + ubytes <= 200 * 1024) ? tbytes : 0);
   if ((e = cudaFuncSetAttribute(server_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv->smem)) !=
       cudaSuccess)

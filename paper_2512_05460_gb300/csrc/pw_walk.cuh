@@ -20,18 +20,21 @@ struct ZOnTheFly {
   }
 };
 
-// Probe entries read from the block's 2-bit table of z^(k) (built once per
-// probe): code bit 0 = nonzero, bit 1 = negative.
+// Probe entries read from the block's table of z^(k) (built once per probe):
+// one sign bit per node (set = negative) plus the ids of the r <= 2 nodes of
+// the zero set, which the bits cannot express.
 struct ZTable {
   const uint32_t* tab;
-  __device__ __forceinline__ static int decode(uint32_t c) { return (int)(c & 1u) - (int)(c & 2u); }
+  uint32_t zero0, zero1;  // zero-set nodes, 0xFFFFFFFF when absent
+  __device__ __forceinline__ int one(uint32_t v) const {
+    const int neg = (int)((tab[v >> 5] >> (v & 31u)) & 1u);
+    return (v == zero0 || v == zero1) ? 0 : 1 - 2 * neg;
+  }
   __device__ __forceinline__ void pair(uint32_t vs, uint32_t vt, int& zs, int& zt) const {
-    zs = decode(tab[vs >> 4] >> ((vs & 15u) << 1));
-    zt = decode(tab[vt >> 4] >> ((vt & 15u) << 1));
+    zs = one(vs);
+    zt = one(vt);
   }
 };
-
-__device__ __forceinline__ uint32_t z_code(int z) { return z == 0 ? 0u : (z > 0 ? 1u : 3u); }
 
 // One replica: walks from s and t interleaved, a and b summed in FP32 in step
 // order (Eq. hatphi-def), U_p = a - b.  The load of X_{i+1} is issued before
@@ -92,27 +95,42 @@ __device__ __forceinline__ float walk_pair(const int4* __restrict__ rec, const i
   }
 }
 
-// z^(k) of every node into a 2-bit shared-memory table (16 nodes per word),
-// one Feistel cycle-walk per node.  Each thread owns whole words and runs a
-// flat queue (one Feistel pass per iteration, moving to its next node when a
-// pass lands in [n]), so lanes stay busy even though cycle-walk lengths vary.
+// Words of the per-probe table: one sign bit per node, then two words for
+// the zero set.
+__host__ __device__ __forceinline__ uint32_t table_words(uint32_t n) { return (n + 31u) / 32u + 2u; }
+
+// z^(k) of every node into the shared-memory table: one Feistel cycle-walk
+// per node.  Each thread owns whole 32-node words and runs a flat queue (one
+// Feistel pass per iteration; it moves to its next node when a pass lands in
+// [n]), so lanes stay busy even though cycle-walk lengths vary.  Nodes of the
+// zero set (pi >= n - r) are listed in the two words after the bits.
 __device__ __forceinline__ void build_probe_table(const Probe& pr, uint32_t* tab, uint32_t n) {
-  const uint32_t nwords = (n + 15u) / 16u;
-  uint32_t w = threadIdx.x, v = w * 16u, x = v, acc = 0;
+  const uint32_t nwords = (n + 31u) / 32u;
+  uint32_t* zero = tab + nwords;
+  if (threadIdx.x < 2) zero[threadIdx.x] = 0xFFFFFFFFu;
+  __syncthreads();
+  uint32_t w = threadIdx.x, v = w * 32u, x = v, acc = 0;
   while (w < nwords) {
     x = feistel_once(pr, x);
     if (x < n) {
-      acc |= z_code(probe_z_from_pi(pr, x)) << ((v & 15u) << 1);
+      const int z = probe_z_from_pi(pr, x);
+      if (z == 0) zero[x - pr.n_active] = v;
+      acc |= (uint32_t)(z < 0) << (v & 31u);
       ++v;
-      if ((v & 15u) == 0 || v >= n) {
+      if ((v & 31u) == 0 || v >= n) {
         tab[w] = acc;
         acc = 0;
         w += blockDim.x;
-        v = w * 16u;
+        v = w * 32u;
       }
       x = v;
     }
   }
+}
+
+__device__ __forceinline__ ZTable table_reader(const uint32_t* tab, uint32_t n) {
+  const uint32_t nwords = (n + 31u) / 32u;
+  return ZTable{tab, tab[nwords], tab[nwords + 1]};
 }
 
 }  // namespace pw
