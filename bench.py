@@ -274,6 +274,86 @@ def run_server(pw, g, s, t, eps, L, seeds, params, want):
     return out
 
 
+def run_stabilized(args, wl, world, rank, local):
+    """Section 4.3: L chosen per query by doubling from L = 1 until the estimate
+    stabilises (cap L_max = 256, the paper's reference length); reports
+    queries/s, the distribution of L_stop and the proxy relative error
+    |beta(L_stop) - beta(L_max)| / |beta(L_max)| of Fig. 3."""
+    import torch
+
+    from paper_2512_05460_gb300 import build as pwbuild
+
+    pwbuild.build()
+    from paper_2512_05460_gb300 import probewalk as pw
+
+    torch.cuda.set_device(local)
+    host, s, t, seeds = workload_inputs(wl, rank)
+    n = args.queries or 200
+    s, t, seeds = s[:n], t[:n], seeds[:n]
+    eps = workload_eps(wl, n, rank)
+    g = pw.Graph(host.row_ptr, host.col_idx, device=local)
+    L_max = 256
+    pw.pw_query_stabilized(g.handle, s[:8], t[:8], eps[:8], L_max, seeds[:8])  # warm-up
+    pw.pw_launch_count(reset=True)
+    t0 = time.perf_counter()
+    beta, L_stop, st = pw.pw_query_stabilized(g.handle, s, t, eps, L_max, seeds)
+    wall = time.perf_counter() - t0
+    launches = pw.pw_launch_count(reset=True)
+    assert np.all(st == 0)
+    ref_seeds = np.array([pw.pw_level_seed(int(x), L_max) for x in seeds], np.uint64)
+    ref, _ = pw.pw_query_batch(g.handle, s, t, eps, np.full(n, L_max, np.int32), ref_seeds)
+    proxy = np.abs(beta - ref) / np.abs(ref)
+    hist = {int(L): int((L_stop == L).sum()) for L in np.unique(L_stop)}
+    line = {"metric": "queries/s with L chosen by the stabilization rule (Section 4.3), L_max=256",
+            "value": n / wall, "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}; {n} uniform pairs; eps={wl['eps']}; "
+                                   f"L_max={L_max}; PILOT budget c_B=0.5"},
+            "L_stop_histogram": hist, "proxy_rel_error": {"median": float(np.median(proxy)),
+                                                          "p95": float(np.percentile(proxy, 95)),
+                                                          "frac_within_eps": float(np.mean(proxy <= eps))},
+            "gpu_launches": launches, "wall_s": wall}
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
+def run_eps_sweep(args, wl, world, rank, local):
+    """Fig. 2's protocol on the synthetic workload: for eps in {0.02, 0.04,
+    0.06, 0.1, 0.2}, mean runtime per query (one batch of the queries, CUDA
+    events) and mean relative error against the oracle's series beta^(L)."""
+    import torch
+
+    from oracle import exact
+    from paper_2512_05460_gb300 import build as pwbuild
+
+    pwbuild.build()
+    from paper_2512_05460_gb300 import probewalk as pw
+
+    torch.cuda.set_device(local)
+    host, s, t, seeds = workload_inputs(wl, rank)
+    n = args.queries or 32
+    s, t, seeds = s[:n], t[:n], seeds[:n]
+    L = wl["L"]
+    ref = exact.series_beta_many(host.row_ptr, host.col_idx, host.n, s, t, L)
+    g = pw.Graph(host.row_ptr, host.col_idx, device=local)
+    pw.pw_query_batch(g.handle, s[:4], t[:4], 0.2, L, seeds[:4])
+    rows = []
+    for e in (0.02, 0.04, 0.06, 0.1, 0.2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        beta, st = pw.pw_query_batch(g.handle, s, t, e, L, seeds)
+        wall = time.perf_counter() - t0
+        assert np.all(st == 0)
+        rel = np.abs(beta - ref) / ref
+        rows.append({"eps": e, "ms_per_query": 1000 * wall / n, "mean_rel_error": float(rel.mean()),
+                     "frac_within_eps": float(np.mean(rel <= e))})
+    line = {"metric": "eps sweep (Fig. 2 protocol): mean runtime per query and mean relative error",
+            "unit": "ms/query", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}; {n} uniform pairs; L={L}; batch of all queries; "
+                                   "reference beta^(L) from the oracle's series"}, "rows": rows}
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
 def run_ours(args, wl, world, rank, local):
     import torch
 
@@ -455,6 +535,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-server", action="store_true")
+    ap.add_argument("--stabilized", action="store_true", help="L by the stabilization rule (Section 4.3)")
+    ap.add_argument("--eps-sweep", action="store_true", help="runtime and error over eps (Fig. 2 protocol)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -462,6 +544,10 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, wl, world, rank)
+    elif args.stabilized:
+        run_stabilized(args, wl, world, rank, local)
+    elif args.eps_sweep:
+        run_eps_sweep(args, wl, world, rank, local)
     else:
         run_ours(args, wl, world, rank, local)
     if world > 1:

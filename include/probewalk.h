@@ -160,6 +160,23 @@ pw_status pw_query_batch_noalloc(pw_graph* g, int64_t count, const int64_t* d_s,
                                  const double* d_eps, const int32_t* d_L, const uint64_t* d_seeds,
                                  const pw_params* params, double* d_beta_hat, int32_t* d_status, void* stream);
 
+/* ---- stabilization rule (Section 4.3) ----------------------------------------
+ * pw_query_stabilized: choose L per query as the paper does on graphs whose
+ * spectral gap is unknown: starting from L = 1, double L (capped at L_max)
+ * and accept L_stop = 2L as soon as |beta(2L) - beta(L)| <= (eps/2) |beta(2L)|;
+ * when L reaches L_max without that, the estimate at L_max is returned with
+ * L_stop = L_max.  Every level is a full run of Algorithm 1 keyed by
+ * pw_level_seed(seed, L) (seeds: host array or NULL for
+ * pw_default_seed(params->seed, s, t, eps, L_max)); all queries still doubling
+ * run in one batch per level.  Host arrays of length count: s, t, eps (in),
+ * beta_hat, L_stop, per_query_status (out).  L_max >= 2.  s == t gives 0. */
+pw_status pw_query_stabilized(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
+                              int32_t L_max, const uint64_t* seeds, const pw_params* params, double* beta_hat,
+                              int32_t* L_stop, int32_t* per_query_status);
+/* Seed of level L of a stabilized query: first two words of Philox4x32-10
+ * keyed by `seed` over the counter (L, 0, 0, 0x57AB). */
+uint64_t pw_level_seed(uint64_t seed, int32_t L);
+
 /* ---- sharded query (one query split across GPUs) ---------------------------
  * pw_query_blocks: the median-of-means blocks [g_begin, g_end) of one query
  * (Eq. final-estimator before the median): the same budget and the same

@@ -92,6 +92,8 @@ def _configure(L):
     L.orc_query_many.argtypes = [i64p, i32p, ctypes.c_int64, ctypes.c_int64, i64p, i64p, dp, i32p, u64p,
                                  P(BudgetCfg), ctypes.c_int, dp, u64p, i32p]
     L.orc_query_many.restype = ctypes.c_int
+    L.orc_level_seed.argtypes = [ctypes.c_uint64, ctypes.c_int32]
+    L.orc_level_seed.restype = ctypes.c_uint64
     L.orc_max_threads.argtypes = []
     L.orc_max_threads.restype = ctypes.c_int
     return L
@@ -260,6 +262,31 @@ def query_many(g, s, t, eps, L, seeds, cfg: BudgetCfg | None = None, threads: in
                          _ptr(seeds, ctypes.c_uint64), ctypes.byref(cfg), threads, _ptr(beta, ctypes.c_double),
                          _ptr(budgets, ctypes.c_uint64), _ptr(status, ctypes.c_int32))
     return beta, budgets, status
+
+
+def level_seed(seed: int, L: int) -> int:
+    return int(lib().orc_level_seed(seed, L))
+
+
+def stabilized(g, s: int, t: int, eps: float, L_max: int, seed: int, cfg: BudgetCfg | None = None):
+    """The stabilization rule of Section 4.3: from L = 1, double L (capped at
+    L_max) and accept L_stop = 2L once |beta(2L) - beta(L)| <= (eps/2)|beta(2L)|;
+    each level is an independent run of Algorithm 1 with seed level_seed(seed, L).
+    Returns (beta_hat, L_stop, per-level estimates)."""
+    if s == t:
+        return 0.0, 1, {}
+    levels = {}
+    L = 1
+    prev = None
+    while True:
+        cur = query(g, s, t, eps, L, level_seed(seed, L), cfg)["beta"]
+        levels[L] = cur
+        if prev is not None and abs(cur - prev) <= eps / 2 * abs(cur):
+            return cur, L, levels
+        if L >= L_max:
+            return cur, L, levels
+        prev = cur
+        L = min(2 * L, L_max)
 
 
 def max_threads() -> int:

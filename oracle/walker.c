@@ -89,6 +89,14 @@ uint64_t orc_default_seed(uint64_t global_seed, int64_t s, int64_t t, double eps
   return (uint64_t)out[0] | ((uint64_t)out[1] << 32);
 }
 
+/* Seed of truncation level L of a stabilized query: Philox block keyed by the
+ * query seed over the counter (L, 0, 0, 0x57AB), first two words. */
+uint64_t orc_level_seed(uint64_t seed, int32_t L) {
+  uint32_t out[4];
+  philox_seeded(seed, (uint32_t)L, 0u, 0u, 0x57ABu, out);
+  return (uint64_t)out[0] | ((uint64_t)out[1] << 32);
+}
+
 /* ---------------------------------------------------------------------------
  * Paired-Sign Probe, stateless generator (Section 3.3).
  * ------------------------------------------------------------------------- */

@@ -150,6 +150,8 @@ pw_status pw_block_median(const double* block_means, int64_t G, double* out) {
   return PW_OK;
 }
 
+uint64_t pw_level_seed(uint64_t seed, int32_t L) { return pw::level_seed(seed, L); }
+
 uint64_t pw_default_seed(uint64_t global_seed, int64_t s, int64_t t, double eps, int32_t L) {
   return pw::default_seed(global_seed, s, t, eps, L);
 }

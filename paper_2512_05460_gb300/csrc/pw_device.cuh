@@ -103,6 +103,14 @@ __host__ __device__ __forceinline__ uint64_t default_seed(uint64_t global_seed, 
   return (uint64_t)o.x | ((uint64_t)o.y << 32);
 }
 
+// Seed of truncation level L of a stabilized query: the first two words of the
+// Philox block keyed by the query seed with counter (L, 0, 0, 0x57AB).
+constexpr uint32_t kTagLevel = 0x57ABu;
+__host__ __device__ __forceinline__ uint64_t level_seed(uint64_t seed, int32_t L) {
+  const Philox4 o = philox_seeded(seed, (uint32_t)L, 0u, 0u, kTagLevel);
+  return (uint64_t)o.x | ((uint64_t)o.y << 32);
+}
+
 // ---- Paired-Sign Probe -------------------------------------------------------
 
 struct Probe {

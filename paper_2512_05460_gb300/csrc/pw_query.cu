@@ -725,6 +725,76 @@ pw_status pw_query_blocks(pw_graph* g, int64_t s, int64_t t, double eps, int32_t
   return st;
 }
 
+pw_status pw_query_stabilized(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
+                              int32_t L_max, const uint64_t* seeds, const pw_params* params, double* beta_hat,
+                              int32_t* L_stop, int32_t* per_query_status) {
+  if (!g) return set_error(PW_ERR_ARG, "graph is NULL");
+  if (count < 0 || L_max < 2) return set_error(PW_ERR_ARG, "count < 0 or L_max < 2");
+  if (count == 0) return PW_OK;
+  if (!s || !t || !eps || !beta_hat || !L_stop || !per_query_status) return set_error(PW_ERR_ARG, "NULL array");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  BudgetArgs ba;
+  pw_status st = resolve_budget(params, g, &ba, nullptr);
+  if (st != PW_OK) return st;
+  const size_t nq = (size_t)count;
+  std::vector<uint64_t> qseed(nq);
+  for (size_t i = 0; i < nq; ++i)
+    qseed[i] = seeds ? seeds[i] : default_seed(ba.global_seed, s[i], t[i], eps[i], L_max);
+  std::vector<double> prev(nq, 0.0);
+  std::vector<int64_t> act;  // queries still doubling
+  for (size_t i = 0; i < nq; ++i) {
+    per_query_status[i] = PW_OK;
+    L_stop[i] = 0;
+    beta_hat[i] = 0.0;
+    if (s[i] == t[i]) {
+      L_stop[i] = 1;
+    } else {
+      act.push_back((int64_t)i);
+    }
+  }
+  std::vector<int64_t> bs, bt;
+  std::vector<double> be, bb;
+  std::vector<int32_t> bL, bst;
+  std::vector<uint64_t> bseed;
+  for (int32_t L = 1; !act.empty(); L = L >= L_max ? L_max : (2 * L > L_max ? L_max : 2 * L)) {
+    const size_t na = act.size();
+    bs.resize(na); bt.resize(na); be.resize(na); bL.assign(na, L); bseed.resize(na); bb.resize(na); bst.resize(na);
+    for (size_t j = 0; j < na; ++j) {
+      const size_t i = (size_t)act[j];
+      bs[j] = s[i];
+      bt[j] = t[i];
+      be[j] = eps[i];
+      bseed[j] = level_seed(qseed[i], L);
+    }
+    st = host_batch(g, (int64_t)na, bs.data(), bt.data(), be.data(), bL.data(), bseed.data(), params, bb.data(),
+                    bst.data(), nullptr);
+    if (st != PW_OK) return st;
+    std::vector<int64_t> next;
+    for (size_t j = 0; j < na; ++j) {
+      const size_t i = (size_t)act[j];
+      if (bst[j] != PW_OK) {
+        per_query_status[i] = bst[j];
+        beta_hat[i] = bb[j];
+        L_stop[i] = L;
+        continue;
+      }
+      // Section 4.3: accept 2L once |beta(2L) - beta(L)| <= (eps/2) |beta(2L)|
+      const bool stable = L > 1 && fabs(bb[j] - prev[i]) <= eps[i] / 2.0 * fabs(bb[j]);
+      if (stable || L >= L_max) {
+        beta_hat[i] = bb[j];
+        L_stop[i] = L;
+      } else {
+        prev[i] = bb[j];
+        next.push_back((int64_t)i);
+      }
+    }
+    act.swap(next);
+    if (L >= L_max) break;
+  }
+  return PW_OK;
+}
+
 pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stats* out) {
   if (!g) return set_error(PW_ERR_ARG, "graph is NULL");
   std::lock_guard<std::mutex> guard(g->lock);

@@ -94,6 +94,9 @@ SIGNATURES = {
                               P(_i32)]),
     "pw_query_batch_device": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, P(pw_params), _vp, _vp, _vp]),
     "pw_query_batch_noalloc": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, P(pw_params), _vp, _vp, _vp]),
+    "pw_query_stabilized": (_i32, [_vp, _i64, P(_i64), P(_i64), P(_dbl), _i32, P(_u64), P(pw_params), P(_dbl),
+                                   P(_i32), P(_i32)]),
+    "pw_level_seed": (_u64, [_u64, _i32]),
     "pw_query_blocks": (_i32, [_vp, _i64, _i64, _dbl, _i32, P(_u64), P(pw_params), _i64, _i64, P(_dbl)]),
     "pw_block_median": (_i32, [P(_dbl), _i64, P(_dbl)]),
     "pw_server_create": (_i32, [_vp, P(pw_params), ctypes.c_size_t, P(_vp)]),
@@ -255,6 +258,26 @@ def pw_query_batch_noalloc(g: int, count: int, d_s, d_t, d_eps, d_L, d_seeds, d_
     _check(lib().pw_query_batch_noalloc(g, count, _dev_ptr(d_s), _dev_ptr(d_t), _dev_ptr(d_eps), _dev_ptr(d_L),
                                         _dev_ptr(d_seeds), _params(params), _dev_ptr(d_beta), _dev_ptr(d_status),
                                         stream))
+
+
+def pw_query_stabilized(g: int, s, t, eps, L_max: int, seeds=None, params=None):
+    """Section 4.3's doubling rule; returns (beta_hat, L_stop, status)."""
+    s = _arr(s, np.int64)
+    n = s.size
+    t = _arr(t, np.int64)
+    eps = _arr(np.broadcast_to(eps, (n,)), np.float64)
+    sd = None if seeds is None else _arr(seeds, np.uint64)
+    beta = np.zeros(n, np.float64)
+    Ls = np.zeros(n, np.int32)
+    st = np.zeros(n, np.int32)
+    _check(lib().pw_query_stabilized(g, n, _p(s, _i64), _p(t, _i64), _p(eps, _dbl), L_max,
+                                     None if sd is None else _p(sd, _u64), _params(params), _p(beta, _dbl),
+                                     _p(Ls, _i32), _p(st, _i32)))
+    return beta, Ls, st
+
+
+def pw_level_seed(seed: int, L: int) -> int:
+    return int(lib().pw_level_seed(seed, L))
 
 
 def pw_query_blocks(g: int, s: int, t: int, eps: float, L: int, g_begin: int, g_end: int, seed=None,

@@ -75,3 +75,10 @@ def test_params_struct_layout(built_lib, tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(built_lib.pw_params)] + [getattr(built_lib.pw_params, f).offset for f in fields]
     assert got == want
+
+
+def test_level_seed_matches_oracle(built_lib):
+    import oracle
+
+    for seed, L in ((1, 1), (2**64 - 1, 256), (987654321, 37)):
+        assert built_lib.pw_level_seed(seed, L) == oracle.level_seed(seed, L)

@@ -312,3 +312,27 @@ def test_sharded_blocks_equal_whole_query(pw, tiny):
         G = pw.pw_budget(g.handle, s, t, 0.2, 32, seed)["G"]
         parts = [pw.pw_query_blocks(g.handle, s, t, 0.2, 32, a, b, seed) for a, b in ((0, 13), (13, 30), (30, G))]
         assert pw.pw_block_median(np.concatenate(parts)) == whole
+
+
+def test_stabilized_matches_oracle(pw, oracle_lib, tiny):
+    """Section 4.3's doubling rule: the library's estimates and L_stop equal the oracle's."""
+    host, g = tiny
+    s, t = uniform_pairs(host.n, 12, 310)
+    seeds = query_seeds(12, 311)
+    s[3] = t[3]  # one query with s == t
+    beta, L_stop, st = pw.pw_query_stabilized(g.handle, s, t, 0.2, 64, seeds)
+    assert np.all(st == 0)
+    for i in range(12):
+        b, Ls, _ = oracle.stabilized(host, int(s[i]), int(t[i]), 0.2, 64, int(seeds[i]))
+        assert beta[i] == b and L_stop[i] == Ls
+
+
+def test_stabilized_ba(pw, oracle_lib, ba):
+    host, g = ba
+    s, t = uniform_pairs(host.n, 4, 320)
+    seeds = query_seeds(4, 321)
+    beta, L_stop, st = pw.pw_query_stabilized(g.handle, s, t, 0.2, 64, seeds)
+    assert np.all(st == 0)
+    for i in range(4):
+        b, Ls, _ = oracle.stabilized(host, int(s[i]), int(t[i]), 0.2, 64, int(seeds[i]))
+        assert beta[i] == b and L_stop[i] == Ls
