@@ -56,10 +56,12 @@ def workload_eps(wl: dict, count: int, rank: int = 0) -> np.ndarray:
 SECTOR_BYTES = 32  # one 16-byte neighbour record per transition lives in one 32-byte sector
 L2_BYTES = 129 << 20
 WALK_KERNEL_NAME = {1: "walk_kernel (per-visit probe evaluation)", 2: "walk_table_kernel (per-probe table)"}
-# DRAM bytes per launch of the walk kernel from the committed ncu capture
-# (profiles/), scaled from the captured case to the full launch by transitions;
-# None until a capture of the current kernel exists.
-WALK_TRAFFIC: dict = {}
+# Per-transition DRAM and L2 bytes of the walk kernel from the committed ncu
+# capture of the current kernel (profiles/walk_table_kernel_ba1e5.md: one
+# launch of 8 BA queries, 6.2515e9 transitions, dram read+write 30.31 MB,
+# lts__t_sectors 6.467e9); scaled to a launch by its transitions.
+WALK_TRAFFIC = {("ba-1e5", 2): {"dram_per_transition": 30.31e6 / 6.2515e9,
+                                "l2_per_transition": 6.467e9 * 32 / 6.2515e9}}
 
 
 def load_peaks():
@@ -471,7 +473,12 @@ def run_ours(args, wl, world, rank, local):
     else:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak, "peak_kind": peak_kind}
-    roofline.update({"traffic": WALK_TRAFFIC.get((args.workload, walk_mode)), "kernel": WALK_KERNEL_NAME[walk_mode],
+    tr = WALK_TRAFFIC.get((args.workload, walk_mode))
+    roofline.update({"traffic": tr and tr["dram_per_transition"] * transitions_per_step,
+                     "l2_traffic": tr and tr["l2_per_transition"] * transitions_per_step,
+                     "traffic_note": tr and "ncu capture of 8 queries scaled by transitions; the DRAM bytes are the "
+                                            "U_p writes, most of which stay in L2 at the captured size",
+                     "kernel": WALK_KERNEL_NAME[walk_mode],
                      "algorithmic_bytes_per_launch": walk_bytes,
                      "bytes_model": "32 B (one sector holding the 16 B neighbour record) per walk transition",
                      "walk_ms_per_launch": walk_ms_avg})
