@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkArgs A) {
 // on-the-fly kernel; cheaper whenever a probe's walks visit more nodes than
 // the graph has (2 R (L+1) > n).
 template <bool DEBUG>
-__global__ void __launch_bounds__(kWalkThreads, 4) walk_table_kernel(WalkArgs A,
+__global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A,
                                                                   const unsigned long long* __restrict__ probe_prefix,
                                                                   unsigned long long* __restrict__ probe_counter) {
   extern __shared__ uint32_t tab[];
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kWalkThreads, 4) walk_table_kernel(WalkArgs A,
       const uint32_t p = c * 32u + lane;
       if (p < R) {
         const uint64_t pair = (uint64_t)k * R + p;
-        const float U = walk_pair<DEBUG>(A.rec, A.node, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
+        const float U = walk_pair_table<DEBUG>(A.rec, A.node, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
         A.u[P.u_begin + (uint64_t)kl * R + p] = U;
       }
     }

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kServerThreads, 5) server_kernel(ServerArgs A)
         float U;
         if (table) {
           const ZTable zp = table_reader(tab, A.n);
-          U = walk_pair<false>(A.rec, A.node, nullptr, walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
+          U = walk_pair_table<false>(A.rec, A.node, nullptr, walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
         } else {
           const ZOnTheFly zp{pr};
           U = walk_pair<false>(A.rec, A.node, nullptr, walk_tag, zp, P.s, P.t, P.L, P.seed, pair);

@@ -26,10 +26,11 @@ struct ZOnTheFly {
 struct ZTable {
   const uint32_t* tab;
   uint32_t zero0, zero1;  // zero-set nodes, 0xFFFFFFFF when absent
-  __device__ __forceinline__ int one(uint32_t v) const {
-    const int neg = (int)((tab[v >> 5] >> (v & 31u)) & 1u);
+  __device__ __forceinline__ int from_word(uint32_t word, uint32_t v) const {
+    const int neg = (int)((word >> (v & 31u)) & 1u);
     return (v == zero0 || v == zero1) ? 0 : 1 - 2 * neg;
   }
+  __device__ __forceinline__ int one(uint32_t v) const { return from_word(tab[v >> 5], v); }
   __device__ __forceinline__ void pair(uint32_t vs, uint32_t vt, int& zs, int& zt) const {
     zs = one(vs);
     zt = one(vt);
@@ -98,6 +99,80 @@ __device__ __forceinline__ float walk_pair(const int4* __restrict__ rec, const i
 // Words of the per-probe table: one sign bit per node, then two words for
 // the zero set.
 __host__ __device__ __forceinline__ uint32_t table_words(uint32_t n) { return (n + 31u) / 32u + 2u; }
+
+// One replica with probe entries from the shared-memory table, software
+// pipelined: at step i the gather of X_{i+1} and the table read of X_i are
+// issued, and the term of X_{i-1} (whose table word was read one step
+// earlier) is added.  The additions keep step order, so the result equals
+// walk_pair's bit for bit.
+template <bool DEBUG>
+__device__ __forceinline__ float walk_pair_table(const int4* __restrict__ rec, const int4* __restrict__ node,
+                                                 uint32_t* visits, uint32_t walk_tag, const ZTable& zt, int32_t s,
+                                                 int32_t t, int32_t L, uint64_t seed, uint64_t pair) {
+  const int4 xs = __ldg(node + s), xt = __ldg(node + t);
+  float a = signed_term(zt.one((uint32_t)xs.x), (uint32_t)xs.w);
+  float b = signed_term(zt.one((uint32_t)xt.x), (uint32_t)xt.w);
+  if (DEBUG) {
+    atomicAdd(visits + xs.x, 1u);
+    atomicAdd(visits + xt.x, 1u);
+  }
+  if (L == 0) return __fsub_rn(a, b);
+  const uint64_t ws = 2 * pair, wt = ws + 1;
+  const PhiloxKeys keys = philox_keys(seed);
+  Philox4 rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), 0u, walk_tag, keys);
+  Philox4 rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), 0u, walk_tag, keys);
+  int4 ns = __ldg(rec + ((uint32_t)xs.y + __umulhi(rs.y, (uint32_t)xs.z)));
+  int4 nt = __ldg(rec + ((uint32_t)xt.y + __umulhi(rt.y, (uint32_t)xt.z)));
+  // pending term: table word, node and reciprocal of the previous step's nodes
+  uint32_t ps_word = 0, pt_word = 0, ps_v = 0xFFFFFFFFu, pt_v = 0xFFFFFFFFu, ps_inv = 0, pt_inv = 0;
+  bool pending = false;
+  for (uint32_t blk = 0;; ++blk) {
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      if (w == 0 && blk == 0) continue;
+      const uint32_t i = blk * 4u + (uint32_t)w;  // ns, nt hold X_i
+      const bool more = i < (uint32_t)L;
+      int4 ns2 = ns, nt2 = nt;
+      if (more) {
+        uint32_t wsw, wtw;
+        if (w == 3) {
+          rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), blk + 1u, walk_tag, keys);
+          rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), blk + 1u, walk_tag, keys);
+          wsw = rs.x;
+          wtw = rt.x;
+        } else {
+          wsw = (w == 0) ? rs.y : (w == 1) ? rs.z : rs.w;
+          wtw = (w == 0) ? rt.y : (w == 1) ? rt.z : rt.w;
+        }
+        ns2 = __ldg(rec + ((uint32_t)ns.y + __umulhi(wsw, (uint32_t)ns.z)));
+        nt2 = __ldg(rec + ((uint32_t)nt.y + __umulhi(wtw, (uint32_t)nt.z)));
+      }
+      const uint32_t cs_word = zt.tab[(uint32_t)ns.x >> 5], ct_word = zt.tab[(uint32_t)nt.x >> 5];
+      if (pending) {
+        a = __fadd_rn(a, signed_term(zt.from_word(ps_word, ps_v), ps_inv));
+        b = __fadd_rn(b, signed_term(zt.from_word(pt_word, pt_v), pt_inv));
+      }
+      if (DEBUG) {
+        atomicAdd(visits + ns.x, 1u);
+        atomicAdd(visits + nt.x, 1u);
+      }
+      ps_word = cs_word;
+      pt_word = ct_word;
+      ps_v = (uint32_t)ns.x;
+      pt_v = (uint32_t)nt.x;
+      ps_inv = (uint32_t)ns.w;
+      pt_inv = (uint32_t)nt.w;
+      pending = true;
+      if (!more) {
+        a = __fadd_rn(a, signed_term(zt.from_word(ps_word, ps_v), ps_inv));
+        b = __fadd_rn(b, signed_term(zt.from_word(pt_word, pt_v), pt_inv));
+        return __fsub_rn(a, b);
+      }
+      ns = ns2;
+      nt = nt2;
+    }
+  }
+}
 
 // z^(k) of every node into the shared-memory table: one Feistel cycle-walk
 // per node.  Each thread owns whole 32-node words and runs a flat queue (one
