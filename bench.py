@@ -38,6 +38,8 @@ WORKLOADS = {
                        eps=0.2, pair_seed=100, seed_seed=200),
     "rmat-20": dict(graph="rmat-20", desc="R-MAT 2^20 ef16 (.57,.19,.19,.05) symmetrised, LCC (seed 2)",
                     queries=1000, L=500, eps=("uniform", 0.05, 0.2), pair_seed=102, seed_seed=1002),
+    "rmat-24": dict(graph="rmat-24", desc="R-MAT 2^24 ef16 (.57,.19,.19,.05) symmetrised, LCC (seed 4), native generator",
+                    queries=1000, L=1000, eps=("uniform", 0.05, 0.2), pair_seed=104, seed_seed=1004),
     "grid-2000": dict(graph="grid-2000", desc="2000x2000 grid, 5% edges deleted, LCC (seed 3), bipartite",
                       queries=1000, L=2000, eps=("choice", 0.05, 0.1, 0.2), pair_seed=103, seed_seed=1003),
 }

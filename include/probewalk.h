@@ -177,6 +177,15 @@ pw_status pw_query_stabilized(pw_graph* g, int64_t count, const int64_t* s, cons
  * keyed by `seed` over the counter (L, 0, 0, 0x57AB). */
 uint64_t pw_level_seed(uint64_t seed, int32_t L);
 
+/* ---- truncated series (Lemma 2.3) --------------------------------------------
+ * pw_series_batch: the deterministic beta^(L)(s,t) = ||h||^2 - (1^T h)^2 / n
+ * with h = sum_{i=0}^{L} P^i D^{-1} (e_s - e_t) (Eq. tr-beta-exp-Liu), the
+ * quantity the paper's PUSH baseline computes, in FP64 by L sparse
+ * matrix-vector products on the GPU, 32 queries of equal L per pass.  Host
+ * arrays of length count: s, t, L (in), beta_L (out).  s == t gives 0. */
+pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const int32_t* L,
+                          double* beta_L);
+
 /* ---- sharded query (one query split across GPUs) ---------------------------
  * pw_query_blocks: the median-of-means blocks [g_begin, g_end) of one query
  * (Eq. final-estimator before the median): the same budget and the same

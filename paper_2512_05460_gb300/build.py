@@ -18,13 +18,13 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libprobewalk.so")
-SOURCES = ["pw_common.cu", "pw_graph.cu", "pw_query.cu", "pw_server.cu"]
+SOURCES = ["pw_common.cu", "pw_graph.cu", "pw_query.cu", "pw_server.cu", "pw_series.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 
 def _flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2,-fopenmp",
                    "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 
 
@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError("nvcc failed: " + " ".join(c))
     tmp = LIB + f".tmp{os.getpid()}"
-    link = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
+    link = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread", "-lgomp"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

@@ -82,30 +82,46 @@ __global__ void __launch_bounds__(256) gather_peak_kernel(const int4* __restrict
 static pw_status validate_csr(int64_t n, const int64_t* rp, const int32_t* col, int64_t nnz, uint32_t flags,
                               int32_t* d_min, int32_t* d_max, int32_t* bipartite) {
   if (rp[0] != 0 || rp[n] != nnz) return set_error(PW_ERR_GRAPH, "row_ptr must start at 0 and end at nnz");
+  for (int64_t v = 0; v < n; ++v)
+    if (rp[v + 1] < rp[v] || rp[v + 1] > nnz)
+      return set_error(PW_ERR_GRAPH, "row_ptr is not monotone within [0, nnz] at node " + std::to_string(v));
+  // per-row checks and symmetry, in parallel; the first offending node is reported
+  int64_t bad_row = INT64_MAX, bad_sym = INT64_MAX;
   int32_t dmn = INT32_MAX, dmx = 0;
+#pragma omp parallel for schedule(dynamic, 4096) reduction(min : dmn, bad_row, bad_sym) reduction(max : dmx)
   for (int64_t v = 0; v < n; ++v) {
     const int64_t a = rp[v], b = rp[v + 1];
-    if (b < a || b > nnz) return set_error(PW_ERR_GRAPH, "row_ptr is not monotone within [0, nnz] at node " + std::to_string(v));
-    if (b == a) return set_error(PW_ERR_GRAPH, "isolated node " + std::to_string(v));
     const int64_t d = b - a;
     dmn = (int32_t)std::min<int64_t>(dmn, d);
     dmx = (int32_t)std::max<int64_t>(dmx, d);
+    bool ok = d > 0;
+    for (int64_t e = a; e < b && ok; ++e) {
+      const int32_t u = col[e];
+      if (u < 0 || u >= n || u == v || (e > a && col[e - 1] >= u)) ok = false;
+    }
+    if (!ok) {
+      bad_row = std::min<int64_t>(bad_row, v);
+      continue;
+    }
+    for (int64_t e = a; e < b; ++e) {
+      const int32_t u = col[e];
+      if (!std::binary_search(col + rp[u], col + rp[u + 1], (int32_t)v)) {
+        bad_sym = std::min<int64_t>(bad_sym, v);
+        break;
+      }
+    }
+  }
+  if (bad_row != INT64_MAX) {
+    const int64_t v = bad_row, a = rp[v], b = rp[v + 1];
+    if (b == a) return set_error(PW_ERR_GRAPH, "isolated node " + std::to_string(v));
     for (int64_t e = a; e < b; ++e) {
       const int32_t u = col[e];
       if (u < 0 || u >= n) return set_error(PW_ERR_GRAPH, "neighbour id out of range in row " + std::to_string(v));
       if (u == v) return set_error(PW_ERR_GRAPH, "self-loop at node " + std::to_string(v));
-      if (e > a && col[e - 1] >= u)
-        return set_error(PW_ERR_GRAPH, "row " + std::to_string(v) + " is not strictly increasing");
     }
+    return set_error(PW_ERR_GRAPH, "row " + std::to_string(v) + " is not strictly increasing");
   }
-  // symmetry: (v,u) present implies (u,v) present
-  for (int64_t v = 0; v < n; ++v) {
-    for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
-      const int32_t u = col[e];
-      if (!std::binary_search(col + rp[u], col + rp[u + 1], (int32_t)v))
-        return set_error(PW_ERR_GRAPH, "edge (" + std::to_string(v) + "," + std::to_string(u) + ") has no reverse");
-    }
-  }
+  if (bad_sym != INT64_MAX) return set_error(PW_ERR_GRAPH, "an edge of node " + std::to_string(bad_sym) + " has no reverse");
   *d_min = dmn;
   *d_max = dmx;
   *bipartite = 0;

@@ -102,7 +102,17 @@ __device__ __forceinline__ QPlan load_plan(const QPlan* p) {
 // idle_ns, so the grid leaves together and the host relaunches all of it when
 // work returns (blocks never leave one by one while others keep working).
 // Device-ring (main stage) work is taken first.
-__device__ bool find_job(const ServerArgs& A, uint32_t& slot, uint32_t& stage, uint32_t& k) {
+// Probes per job: one when the main stage reads a per-probe table (a block
+// builds one table at a time), else enough probes for about 8 tiles of 32
+// replicas, so every warp of the block has work when R is small.
+__device__ __forceinline__ uint32_t probes_per_job(const SlotDev* S, uint32_t stage) {
+  const uint32_t R = stage == kStagePilot ? __ldcg(&S->R0) : __ldcg(&S->plan.R);
+  if (stage == kStageMain && __ldcg(&S->use_table)) return 1u;
+  const uint32_t chunks = (R + 31u) / 32u;
+  return chunks >= 8u ? 1u : 8u / chunks;
+}
+
+__device__ bool find_job(const ServerArgs& A, uint32_t& slot, uint32_t& stage, uint32_t& k, uint32_t& count) {
   for (uint32_t it = 0; it < (1u << 28); ++it) {
     if (ld_volatile(A.exit_flag) || ld_volatile(A.stop)) return false;
     bool retry = false;
@@ -114,11 +124,13 @@ __device__ bool find_job(const ServerArgs& A, uint32_t& slot, uint32_t& stage, u
       const uint32_t sg = ld_volatile(A.ring_stage + idx);
       SlotDev* S = A.slots + sl;
       const uint32_t K = __ldcg(&S->K[sg]);
-      const uint32_t kk = atomicAdd(&S->next[sg], 1u);
+      const uint32_t want = probes_per_job(S, sg);
+      const uint32_t kk = atomicAdd(&S->next[sg], want);
       if (kk < K) {
         slot = sl;
         stage = sg;
         k = kk;
+        count = (K - kk < want) ? K - kk : want;
         atomicMax(A.last_claim, global_ns());
         return true;
       }
@@ -137,61 +149,68 @@ __device__ bool find_job(const ServerArgs& A, uint32_t& slot, uint32_t& stage, u
   return false;
 }
 
-__global__ void __launch_bounds__(kServerThreads, 5) server_kernel(ServerArgs A) {
+// TABLE: the graph's probe table fits in shared memory, so main-stage jobs may
+// use it (4 blocks/SM); without it only per-visit jobs exist and the kernel
+// keeps the registers that path needs (no occupancy cap).
+template <bool TABLE>
+__global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(ServerArgs A) {
   extern __shared__ uint32_t smem[];
   uint32_t* tab = smem;
   float* su = (float*)(smem + A.table_words);
   double* means = (double*)su;
-  __shared__ uint32_t j_slot, j_stage, j_k, j_valid, j_last, j_tile;
+  __shared__ uint32_t j_slot, j_stage, j_k, j_count, j_valid, j_last, j_tile;
   const uint32_t lane = threadIdx.x & 31u;
   if (threadIdx.x == 0) atomicMax(A.last_claim, global_ns());  // a fresh launch starts its idle clock
   for (;;) {
     if (threadIdx.x == 0) {
-      uint32_t sl = 0, sg = 0, kk = 0;
-      j_valid = find_job(A, sl, sg, kk) ? 1u : 0u;
+      uint32_t sl = 0, sg = 0, kk = 0, cnt = 0;
+      j_valid = find_job(A, sl, sg, kk, cnt) ? 1u : 0u;
       j_slot = sl;
       j_stage = sg;
       j_k = kk;
+      j_count = cnt;
       j_tile = 0;
       j_last = 0;
     }
     __syncthreads();
     if (!j_valid) return;
-    const uint32_t slot = j_slot, stage = j_stage, k = j_k;
+    const uint32_t slot = j_slot, stage = j_stage, k0 = j_k, nprobe = j_count;
     SlotDev* S = A.slots + slot;
     const QPlan P = load_plan(&S->plan);
     const bool pilot = stage == kStagePilot;
     const uint32_t R = pilot ? __ldcg(&S->R0) : P.R;
     const uint32_t walk_tag = pilot ? kTagWalkPilot : kTagWalk;
     const uint32_t probe_tag = pilot ? kTagProbePilot : kTagProbe;
-    const bool table = !pilot && __ldcg(&S->use_table) != 0u;
+    const bool table = TABLE && !pilot && __ldcg(&S->use_table) != 0u;  // then nprobe == 1
     const uint32_t chunks = (R + 31u) / 32u;
-    const Probe pr = make_probe(A.n, P.seed, k, probe_tag);
-    if (table) build_probe_table(pr, tab, A.n);
+    if (TABLE && table) build_probe_table(make_probe(A.n, P.seed, k0, probe_tag), tab, A.n);
     __syncthreads();
+    // tiles of 32 replicas over the job's probes; U_p of probe k0 + j at su[j R + p]
     for (;;) {
       uint32_t c = 0;
       if (lane == 0) c = atomicAdd(&j_tile, 1u);
       c = __shfl_sync(0xffffffffu, c, 0);
-      if (c >= chunks) break;
-      const uint32_t p = c * 32u + lane;
+      if (c >= chunks * nprobe) break;
+      const uint32_t j = c / chunks, p = (c - j * chunks) * 32u + lane;
+      const uint32_t k = k0 + j;
       if (p < R) {
         const uint64_t pair = (uint64_t)k * R + p;
         float U;
-        if (table) {
+        if (TABLE && table) {
           const ZTable zp = table_reader(tab, A.n);
           U = walk_pair_table<false>(A.rec, A.node, nullptr, walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
         } else {
-          const ZOnTheFly zp{pr};
+          const ZOnTheFly zp{make_probe(A.n, P.seed, k, probe_tag)};
           U = walk_pair<false>(A.rec, A.node, nullptr, walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
         }
-        su[p] = U;
+        su[j * R + p] = U;
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < nprobe) {  // one thread per probe: S1, S2 in replica order
+      const uint32_t j = threadIdx.x, k = k0 + j;
       double S1 = 0.0, S2 = 0.0;
-      for (uint32_t p = 0; p < R; ++p) accumulate_s(S1, S2, su[p]);
+      for (uint32_t p = 0; p < R; ++p) accumulate_s(S1, S2, su[j * R + p]);
       if (pilot) {
         __stcg(S->ps + 2 * k, S1);
         __stcg(S->ps + 2 * k + 1, S2);
@@ -199,8 +218,11 @@ __global__ void __launch_bounds__(kServerThreads, 5) server_kernel(ServerArgs A)
         __stcg(S->q + k, u_statistic(S1, S2, R));
       }
       __threadfence();
-      const uint32_t old = atomicAdd(&S->done[stage], 1u);
-      j_last = (old + 1u == __ldcg(&S->K[stage])) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const uint32_t old = atomicAdd(&S->done[stage], nprobe);
+      j_last = (old + nprobe == __ldcg(&S->K[stage])) ? 1u : 0u;
       if (j_last) __threadfence();
     }
     __syncthreads();
@@ -478,7 +500,10 @@ static void worker_loop(pw_server* sv) {
         cudaStreamWaitEvent(sv->kstream, ev, 0);
         cudaEventDestroy(ev);
         cudaMemsetAsync(sv->d_ctl + 4, 0, sizeof(unsigned long long), sv->kstream);  // exit flag
-        server_kernel<<<sv->grid, kServerThreads, sv->smem, sv->kstream>>>(args);
+        if (args.table_words > 0)
+          server_kernel<true><<<sv->grid, kServerThreads, sv->smem, sv->kstream>>>(args);
+        else
+          server_kernel<false><<<sv->grid, kServerThreads, sv->smem, sv->kstream>>>(args);
         count_launch();
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -558,11 +583,16 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
   // rounded to 16 bytes so the U_p area that follows (reused for FP64 block means) stays aligned
   const size_t tbytes = (sizeof(uint32_t) * (size_t)table_words((uint32_t)g->n) + 15) & ~(size_t)15;
   sv->smem = ubytes + ((tbytes + ubytes <= 200 * 1024) ? tbytes : 0);
-  if ((e = cudaFuncSetAttribute(server_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv->smem)) !=
-      cudaSuccess)
+  const bool with_table = sv->smem > ubytes;
+  if ((e = with_table ? cudaFuncSetAttribute(server_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sv->smem)
+                      : cudaFuncSetAttribute(server_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sv->smem)) != cudaSuccess)
     return fail(cuda_error(e, "server smem attribute"));
   int nb = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, server_kernel, kServerThreads, sv->smem)) != cudaSuccess)
+  if ((e = with_table ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, server_kernel<true>, kServerThreads, sv->smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, server_kernel<false>, kServerThreads,
+                                                                      sv->smem)) != cudaSuccess)
     return fail(cuda_error(e, "server occupancy"));
   sv->grid = g->sm_count * (nb > 0 ? nb : 1);
   cudaDeviceSynchronize();

@@ -56,9 +56,11 @@ __device__ __forceinline__ float walk_pair(const int4* __restrict__ rec, const i
   }
   if (L == 0) return __fsub_rn(a, b);
   const uint64_t ws = 2 * pair, wt = ws + 1;
-  const PhiloxKeys keys = philox_keys(seed);
-  Philox4 rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), 0u, walk_tag, keys);
-  Philox4 rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), 0u, walk_tag, keys);
+  // Philox key schedule computed inside each call: this path already holds the
+  // probe's Feistel keys, so hoisting the ten round keys would cost registers
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  Philox4 rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), 0u, walk_tag, k0, k1);
+  Philox4 rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), 0u, walk_tag, k0, k1);
   int4 ns = __ldg(rec + ((uint32_t)xs.y + __umulhi(rs.y, (uint32_t)xs.z)));
   int4 nt = __ldg(rec + ((uint32_t)xt.y + __umulhi(rt.y, (uint32_t)xt.z)));
   for (uint32_t blk = 0;; ++blk) {
@@ -71,8 +73,8 @@ __device__ __forceinline__ float walk_pair(const int4* __restrict__ rec, const i
       if (more) {
         uint32_t wsw, wtw;
         if (w == 3) {
-          rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), blk + 1u, walk_tag, keys);
-          rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), blk + 1u, walk_tag, keys);
+          rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), blk + 1u, walk_tag, k0, k1);
+          rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), blk + 1u, walk_tag, k0, k1);
           wsw = rs.x;
           wtw = rt.x;
         } else {

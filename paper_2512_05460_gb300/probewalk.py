@@ -97,6 +97,7 @@ SIGNATURES = {
     "pw_query_stabilized": (_i32, [_vp, _i64, P(_i64), P(_i64), P(_dbl), _i32, P(_u64), P(pw_params), P(_dbl),
                                    P(_i32), P(_i32)]),
     "pw_level_seed": (_u64, [_u64, _i32]),
+    "pw_series_batch": (_i32, [_vp, _i64, P(_i64), P(_i64), P(_i32), P(_dbl)]),
     "pw_query_blocks": (_i32, [_vp, _i64, _i64, _dbl, _i32, P(_u64), P(pw_params), _i64, _i64, P(_dbl)]),
     "pw_block_median": (_i32, [P(_dbl), _i64, P(_dbl)]),
     "pw_server_create": (_i32, [_vp, P(pw_params), ctypes.c_size_t, P(_vp)]),
@@ -278,6 +279,17 @@ def pw_query_stabilized(g: int, s, t, eps, L_max: int, seeds=None, params=None):
 
 def pw_level_seed(seed: int, L: int) -> int:
     return int(lib().pw_level_seed(seed, L))
+
+
+def pw_series_batch(g: int, s, t, L):
+    """Deterministic beta^(L) by the truncated series (Lemma 2.3), FP64, on the GPU."""
+    s = _arr(s, np.int64)
+    n = s.size
+    t = _arr(t, np.int64)
+    L = _arr(np.broadcast_to(L, (n,)), np.int32)
+    out = np.zeros(n, np.float64)
+    _check(lib().pw_series_batch(g, n, _p(s, _i64), _p(t, _i64), _p(L, _i32), _p(out, _dbl)))
+    return out
 
 
 def pw_query_blocks(g: int, s: int, t: int, eps: float, L: int, g_begin: int, g_end: int, seed=None,

@@ -16,6 +16,7 @@ from .graphs import (  # noqa: F401
     grid_deleted,
     path_graph,
     rmat,
+    rmat_native,
     workload_graph,
 )
 from .queries import (  # noqa: F401

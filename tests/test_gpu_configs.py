@@ -54,3 +54,14 @@ def test_grid_sampled_probes(pw, oracle_lib):
     s, t = uniform_pairs(host.n, 4, 103)
     eps = eps_choice(4, [0.05, 0.1, 0.2], 103)
     _sampled_parity(pw, host, s, t, eps, np.full(4, 2000, np.int32), query_seeds(4, 1003))
+
+
+def test_rmat24_sampled_probes(pw, oracle_lib):
+    """The scale configuration: R-MAT 2^24 (native generator, ~2.7e8 CSR entries,
+    4.3 GB of records), L = 1000, eps uniform in [0.05, 0.2]."""
+    from pw_inputs import rmat_native
+
+    host = rmat_native(24, 16, (0.57, 0.19, 0.19, 0.05), 4)
+    s, t = uniform_pairs(host.n, 3, 104)
+    eps = eps_uniform(3, 0.05, 0.2, 104)
+    _sampled_parity(pw, host, s, t, eps, np.full(3, 1000, np.int32), query_seeds(3, 1004), n_sel=4)

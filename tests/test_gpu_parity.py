@@ -336,3 +336,18 @@ def test_stabilized_ba(pw, oracle_lib, ba):
     for i in range(4):
         b, Ls, _ = oracle.stabilized(host, int(s[i]), int(t[i]), 0.2, 64, int(seeds[i]))
         assert beta[i] == b and L_stop[i] == Ls
+
+
+def test_series_matches_oracle(pw, oracle_lib, tiny, ba):
+    """pw_series_batch against the oracle's series (Lemma 2.3); FP64 sums in a
+    different order, so within 1e-9 relative (n u ~ 1e-11 for n = 1e5)."""
+    for host, g in (tiny, ba):
+        s, t = uniform_pairs(host.n, 40, 330)
+        L = np.array([0, 1, 5, 32] * 10, np.int32)
+        got = pw.pw_series_batch(g.handle, s, t, L)
+        for Lv in (0, 1, 5, 32):
+            m = L == Lv
+            want = exact.series_beta_many(host.row_ptr, host.col_idx, host.n, s[m], t[m], int(Lv))
+            np.testing.assert_allclose(got[m], want, rtol=1e-9, atol=0)
+    host, g = tiny
+    assert pw.pw_series_batch(g.handle, [3], [3], [10])[0] == 0.0

@@ -155,3 +155,20 @@ def test_server_idle_exit_and_relaunch(pw, tiny):
     q = _queries(host.n, 6, 1200)
     want, _ = pw.pw_query_batch(g.handle, *q)
     np.testing.assert_array_equal(_serve(pw, g, *q, gap_s=0.02), want)
+
+
+def test_server_drain_times_out_then_completes(pw):
+    """A wait that runs out returns PW_ERR_TIMEOUT and leaves the server usable."""
+    host = barabasi_albert(100_000, 5, 1)
+    with pw.Graph(host.row_ptr, host.col_idx) as g:
+        srv = pw.pw_server_create(g.handle, None, 1 << 28)
+        try:
+            tk = pw.pw_server_submit(srv, 10, 20000, 0.05, 200, 4242)
+            with pytest.raises(pw.PWError) as e:
+                pw.pw_server_drain(srv, 1)
+            assert e.value.status == pw.PW_ERR_TIMEOUT
+            pw.pw_server_drain(srv, 600000)
+            st, b = pw.pw_server_poll(srv, tk)
+            assert st == pw.PW_OK and b == pw.pw_query(g.handle, 10, 20000, 0.05, 200, 4242)
+        finally:
+            pw.pw_server_destroy(srv)
