@@ -149,6 +149,18 @@ __device__ bool find_job(const ServerArgs& A, uint32_t& slot, uint32_t& stage, u
   return false;
 }
 
+// One per-visit replica (probe entries by Feistel at each visit), compiled as a
+// separate function.  Inlined into the job loop below, the same code ran about
+// 20x slower per walk step on a 4M-node grid (identical results); behind a call
+// boundary it runs at walk_kernel's speed.
+__device__ __noinline__ float server_walk_visit(const int4* __restrict__ rec, const int4* __restrict__ node,
+                                                uint32_t n, uint32_t walk_tag, uint32_t probe_tag, int32_t s,
+                                                int32_t t, int32_t L, uint64_t seed, uint32_t k, uint64_t pair) {
+  const Probe pr = make_probe(n, seed, k, probe_tag);
+  const ZOnTheFly zp{pr};
+  return walk_pair<false>(rec, node, nullptr, walk_tag, zp, s, t, L, seed, pair);
+}
+
 // TABLE: the graph's probe table fits in shared memory, so main-stage jobs may
 // use it (4 blocks/SM); without it only per-visit jobs exist and the kernel
 // keeps the registers that path needs (no occupancy cap).
@@ -200,8 +212,7 @@ __global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(S
           const ZTable zp = table_reader(tab, A.n);
           U = walk_pair_table<false>(A.rec, A.node, nullptr, walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
         } else {
-          const ZOnTheFly zp{make_probe(A.n, P.seed, k, probe_tag)};
-          U = walk_pair<false>(A.rec, A.node, nullptr, walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
+          U = server_walk_visit(A.rec, A.node, A.n, walk_tag, probe_tag, P.s, P.t, P.L, P.seed, k, pair);
         }
         su[j * R + p] = U;
       }
