@@ -59,11 +59,22 @@ SECTOR_BYTES = 32  # one 16-byte neighbour record per transition lives in one 32
 L2_BYTES = 129 << 20
 WALK_KERNEL_NAME = {1: "walk_kernel (per-visit probe evaluation)", 2: "walk_table_kernel (per-probe table)"}
 # Per-transition DRAM and L2 bytes of the walk kernel from the committed ncu
-# capture of the current kernel (profiles/walk_table_kernel_ba1e5.md: one
-# launch of 8 BA queries, 6.2515e9 transitions, dram read+write 30.31 MB,
-# lts__t_sectors 6.467e9); scaled to a launch by its transitions.
-WALK_TRAFFIC = {("ba-1e5", 2): {"dram_per_transition": 30.31e6 / 6.2515e9,
-                                "l2_per_transition": 6.467e9 * 32 / 6.2515e9}}
+# captures of the current kernels, scaled to a launch by its transitions:
+#   profiles/walk_table_kernel_ba1e5.md: one launch of 8 BA queries, 6.2515e9
+#     transitions, dram read+write 30.31 MB, lts__t_sectors 6.467e9;
+#   profiles/walk_kernel_rmat20.md: one per-visit launch of 8 R-MAT 2^20
+#     queries, 1.549856e9 transitions, dram 161.70 GB + 11.27 MB,
+#     lts__t_sectors 8.459e9.
+WALK_TRAFFIC = {
+    ("ba-1e5", 2): {"dram_per_transition": 30.31e6 / 6.2515e9,
+                    "l2_per_transition": 6.467e9 * 32 / 6.2515e9,
+                    "note": "ncu capture of 8 queries scaled by transitions; the DRAM bytes are the U_p writes, "
+                            "most of which stay in L2 at the captured size"},
+    ("rmat-20", 1): {"dram_per_transition": (161.701279e9 + 11.265792e6) / 1.549856e9,
+                     "l2_per_transition": 8459373099 * 32 / 1.549856e9,
+                     "note": "ncu capture of 8 queries scaled by transitions; each 16-B record gather (one sector "
+                             "requested) costs about 3.3 sectors of DRAM reads"},
+}
 
 
 def load_peaks():
@@ -389,6 +400,13 @@ def run_ours(args, wl, world, rank, local):
     def step():
         pw.pw_query_batch_device(g.handle, nq, d_s, d_t, d_eps, d_L, d_seed, d_beta, d_status, params, stream=stream)
 
+    # walk-kernel cost model fitted on this graph (outside every timed region)
+    tune = None
+    if args.walk_mode == 0 and not args.no_autotune:
+        k = min(nq, 8)
+        tune = pw.pw_autotune(g.handle, s[:k], t[:k], eps[:k], L[:k], seeds[:k], params)
+        tune["sample"] = f"first {k} queries of the batch"
+
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
             flush.fill_(i & 0xFF)
@@ -473,13 +491,19 @@ def run_ours(args, wl, world, rank, local):
                     "peak_kind": "measured in this run: dependent random 16-B gathers over the same record array "
                                  "(pw_debug_gather_peak)"}
     else:
+        # Context beside the copy peak: the ceiling of this access pattern
+        # (dependent random 16-B gathers, uniform over the same records, which
+        # is where a stationary walk's transitions land), measured in this run.
+        gather = pw.pw_debug_gather_peak(g.handle, 512) * SECTOR_BYTES / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "peak_kind": peak_kind}
+                    "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                    "gather_ceiling": gather, "frac_of_gather_ceiling": achieved / gather,
+                    "gather_ceiling_kind": "measured in this run: dependent random 16-B gathers uniform over the "
+                                           "same record array (pw_debug_gather_peak)"}
     tr = WALK_TRAFFIC.get((args.workload, walk_mode))
     roofline.update({"traffic": tr and tr["dram_per_transition"] * transitions_per_step,
                      "l2_traffic": tr and tr["l2_per_transition"] * transitions_per_step,
-                     "traffic_note": tr and "ncu capture of 8 queries scaled by transitions; the DRAM bytes are the "
-                                            "U_p writes, most of which stay in L2 at the captured size",
+                     "traffic_note": tr and tr["note"],
                      "kernel": WALK_KERNEL_NAME[walk_mode],
                      "algorithmic_bytes_per_launch": walk_bytes,
                      "bytes_model": "32 B (one sector holding the 16 B neighbour record) per walk transition",
@@ -511,6 +535,7 @@ def run_ours(args, wl, world, rank, local):
                        "parallelism": f"query sharding x{world}"},
             "walk_steps_per_s": walk_steps_per_s,
             "walk_kernel": {1: "per-visit probe evaluation", 2: "per-probe shared-memory table"}.get(walk_mode, "?"),
+            "autotune": tune,
             "transitions_per_step": transitions_per_step,
             "plain_queries_per_s": plain_qps, "plain_sample": plain_n,
             "batched_over_plain": (value / world) / plain_qps if plain_qps else None,
@@ -538,7 +563,9 @@ def main():
     ap.add_argument("--plain", type=int, default=64, help="queries timed in the one-query-per-launch form")
     ap.add_argument("--c_B", type=float, default=0.0)
     ap.add_argument("--queries", type=int, default=0, help="use only the first N queries (small profiling runs)")
-    ap.add_argument("--walk-mode", type=int, default=0, help="0 autotuned, 1 per-visit, 2 probe table")
+    ap.add_argument("--walk-mode", type=int, default=0,
+                    help="0 auto (cost model fitted by pw_autotune on the first 8 queries), 1 per-visit, 2 probe table")
+    ap.add_argument("--no-autotune", action="store_true", help="auto mode with the untuned default cost model")
     ap.add_argument("--cpu-threads", type=int, default=0)
     ap.add_argument("--cpu-probes", type=int, default=40, help="probes per sampled query in the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -73,7 +73,7 @@ typedef struct pw_params {
   uint64_t B, G, R;        /* FIXED mode values (B >= 1, G >= 1, R >= 2) */
   uint64_t R_max;          /* PILOT / SCALED clamp; 0 -> 4096 */
   uint64_t seed;           /* global seed for queries that pass no seed */
-  int32_t walk_mode;       /* 0 autotuned; 1 probe entries evaluated per visit; 2 per-probe shared-memory table */
+  int32_t walk_mode;       /* 0 auto (graph cost model, see pw_autotune); 1 probe entries evaluated per visit; 2 per-probe shared-memory table */
   int32_t reserved1;
 } pw_params;
 
@@ -273,6 +273,38 @@ typedef struct pw_profile_stats {
   int32_t reserved;
 } pw_profile_stats;
 pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stats* out);
+
+/* Walk-kernel autotuner (implementation choice; the paper prescribes what the
+ * walks compute, Algorithm 1, not which kernel runs them).  Both walk kernels
+ * give bit-identical results, so the choice only changes speed.
+ *
+ * Runs the caller's sample batch (host arrays as in pw_query_batch, seeds may
+ * be NULL) three times through the walk kernels, each after one untimed
+ * warm-up: per-visit probe evaluation at the given L, and the per-probe
+ * shared-memory table at L and at L/4 (4 L where L < 4).  From the main walk
+ * kernel's CUDA-event time of each run it fits
+ *   per-visit:  t = visits * visit_ns
+ *   table:      t = probes * table_probe_ns + visits * table_visit_ns
+ * (visits = 2 K R (L+1) summed over the batch) and stores the costs in the
+ * graph: from then on walk_mode 0 (auto) in pw_query*, and servers created
+ * afterwards, use the table when probes * table_probe_ns < visits *
+ * (visit_ns - table_visit_ns).  Costs are whole-GPU nanoseconds, so the sample
+ * should fill the GPU (a few thousand probes).  When the graph's table does not
+ * fit in shared memory (one bit per node in at most 200 KB: n > 1,638,336) only
+ * the per-visit run is made and
+ * table_available = 0; the model then always picks per-visit.  params as in
+ * pw_query (its walk_mode is ignored).  Errors as pw_query_batch; the
+ * estimates of the runs are discarded. */
+typedef struct pw_tune_result {
+  double visit_ns;         /* per-visit kernel, ns per visit */
+  double table_visit_ns;   /* table kernel, ns per visit (0 when unavailable) */
+  double table_probe_ns;   /* table kernel, ns per probe for the table build (0 when unavailable) */
+  double sample_ms[3];     /* walk-kernel time of each timed run (per-visit; table at L; table at L/4) */
+  int32_t table_available; /* 1 when the probe table fits in shared memory */
+  int32_t sample_mode;     /* walk kernel the fitted model picks for the sample: 1 per-visit, 2 table */
+} pw_tune_result;
+pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
+                      const int32_t* L, const uint64_t* seeds, const pw_params* params, pw_tune_result* out);
 
 /* Kernel launches issued by this thread since the last call (instrumentation). */
 uint64_t pw_launch_count(int reset);

@@ -212,6 +212,7 @@ static pw_status load_common(int64_t n, const int64_t* rp, const int32_t* col, i
   g->device = device;
   g->n = n;
   g->nnz = nnz;
+  g->table_probe_cost = (double)n;
   g->d_min = dmn;
   g->d_max = dmx;
   g->bipartite = bip;

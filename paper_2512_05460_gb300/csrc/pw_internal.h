@@ -82,6 +82,13 @@ struct pw_graph {
   std::vector<int32_t> deg;  // host copy of the degrees (host-side query planning)
   int sm_count = 0;
   int last_walk_mode = 0;  // walk kernel chosen by the last batch (1 on-the-fly, 2 table)
+  // Walk-mode cost model: the probe-table kernel is chosen when
+  //   probes * table_probe_cost < visits * table_visit_gain.
+  // Defaults (set at load): n and 2.5, in units of one Feistel pass per node
+  // (table) against about 2.5 passes per visit (per-visit evaluation);
+  // pw_autotune replaces them by nanoseconds measured on this graph.
+  double table_probe_cost = 0.0, table_visit_gain = 2.5;
+  int tuned = 0;
   int4* d_rec = nullptr;   // nnz neighbour records
   int4* d_node = nullptr;  // n node records
   cudaStream_t stream = nullptr;
@@ -112,6 +119,9 @@ struct DebugOut {
   int64_t g_begin = -1;        // >= 0: run only median-of-means blocks [g_begin, g_end) of query 0
   int64_t g_end = -1;
   double* block_means = nullptr;  // device, g_end - g_begin block means (instead of the median)
+  bool time_walk = false;         // record the main walk kernel's duration and the batch totals below
+  float walk_ms = 0.f;
+  unsigned long long n_probes = 0, n_visits = 0;  // K and 2 sum K R (L+1) of the batch
 };
 pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t, const double* d_eps,
                     const int32_t* d_L, const uint64_t* d_seeds, const pw_params* params, double* d_beta,

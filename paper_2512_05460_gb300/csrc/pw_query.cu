@@ -355,6 +355,21 @@ static int table_grid(pw_graph* g, bool debug, size_t smem) {
   return g->sm_count * (nb > 0 ? nb : 1);
 }
 
+// Walk kernel of a batch: the caller's walk_mode, else the graph's cost model
+// (probe table when probes * table_probe_cost < visits * table_visit_gain,
+// 2 R (L+1) visits per probe); the table needs its bits in shared memory.
+static int pick_walk_mode(const pw_graph* g, const pw_params* params, const Totals& T) {
+  int mode = params ? params->walk_mode : 0;
+  if (mode == 0) {
+    const double visits = 2.0 * ((double)T.steps + (double)T.u_slots);
+    mode = (table_bytes(g) <= kMaxTableBytes && (double)T.probes * g->table_probe_cost < visits * g->table_visit_gain)
+               ? 2
+               : 1;
+  }
+  if (mode == 2 && table_bytes(g) > kMaxTableBytes) mode = 1;
+  return mode;
+}
+
 static pw_status launch_walk_table(pw_graph* g, cudaStream_t stream, bool debug, const WalkArgs& a,
                                    const unsigned long long* probe_prefix, unsigned long long* probe_counter) {
   const size_t smem = table_bytes(g);
@@ -464,24 +479,31 @@ pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_
   wa.visits = debug ? dbg->visits : nullptr;
   wa.walk_tag = kTagWalk;
   wa.probe_tag = kTagProbe;
-  // Mode: the probe-table kernel pays n Feistel cycle-walks per probe, the
-  // on-the-fly kernel about 2.5 per visit (2 R (L+1) visits per probe).
-  int mode = params ? params->walk_mode : 0;
-  if (mode == 0) {
-    const double table_cost = (double)T.probes * (double)g->n;
-    const double visit_cost = 2.5 * 2.0 * ((double)T.steps + (double)T.u_slots);
-    mode = (table_bytes(g) <= kMaxTableBytes && table_cost < visit_cost) ? 2 : 1;
-  }
-  if (mode == 2 && table_bytes(g) > kMaxTableBytes) mode = 1;
+  const int mode = pick_walk_mode(g, params, T);
   g->last_walk_mode = mode;
   cudaEvent_t ev_walk;
   prof_begin(g, stream, &ev_walk);
+  cudaEvent_t tw[2] = {nullptr, nullptr};
+  if (dbg && dbg->time_walk) {
+    dbg->n_probes = T.probes;
+    dbg->n_visits = 2ull * (T.steps + T.u_slots);
+    PW_CUDA_TRY(cudaEventCreate(&tw[0]));
+    PW_CUDA_TRY(cudaEventCreate(&tw[1]));
+    PW_CUDA_TRY(cudaEventRecord(tw[0], stream));
+  }
   if (T.tiles > 0) {
     if (mode == 2)
       st = launch_walk_table(g, stream, debug, wa, prefix + nq + 1, counters + 2);
     else
       st = launch_walk(g, stream, debug, wa);
     if (st != PW_OK) return st;
+  }
+  if (tw[0]) {
+    PW_CUDA_TRY(cudaEventRecord(tw[1], stream));
+    PW_CUDA_TRY(cudaEventSynchronize(tw[1]));
+    PW_CUDA_TRY(cudaEventElapsedTime(&dbg->walk_ms, tw[0], tw[1]));
+    cudaEventDestroy(tw[0]);
+    cudaEventDestroy(tw[1]);
   }
   prof_end(g, stream, ev_walk, 0);
   if (g->prof.enabled) {
@@ -828,6 +850,86 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
   return PW_OK;
 }
 
+// Walk-kernel autotuner: time the sample in each walk kernel and fit the
+// graph's cost model (per-visit: visits * visit_ns; table: probes * probe_ns +
+// visits * table_visit_ns).  The two table runs differ only in L, which moves
+// the visits but not the probes (K depends on eps alone), so the pair of
+// timings separates the table build from the table walks.
+pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
+                      const int32_t* L, const uint64_t* seeds, const pw_params* params, pw_tune_result* out) {
+  if (!g || !out) return set_error(PW_ERR_ARG, "NULL argument");
+  if (count <= 0) return set_error(PW_ERR_ARG, "pw_autotune needs a non-empty sample");
+  if (!s || !t || !eps || !L) return set_error(PW_ERR_ARG, "NULL array");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  memset(out, 0, sizeof *out);
+  pw_params p;
+  if (params)
+    p = *params;
+  else
+    memset(&p, 0, sizeof p);
+  const size_t nq = (size_t)count;
+  std::vector<double> beta(nq);
+  std::vector<int32_t> status(nq);
+  std::vector<int32_t> L4(nq);
+  for (size_t i = 0; i < nq; ++i) L4[i] = L[i] >= 4 ? L[i] / 4 : 4 * L[i];
+  // one warm-up and one timed run of the sample in walk kernel `mode`
+  auto timed = [&](int mode, const int32_t* Ls, DebugOut* d) -> pw_status {
+    p.walk_mode = mode;
+    for (int rep = 0; rep < 2; ++rep) {
+      *d = DebugOut();
+      d->time_walk = true;
+      const pw_status st = host_batch(g, count, s, t, eps, Ls, seeds, &p, beta.data(), status.data(), d);
+      if (st != PW_OK) return st;
+    }
+    for (size_t i = 0; i < nq; ++i)
+      if (status[i] != PW_OK) return set_error((pw_status)status[i], "pw_autotune: a sample query failed");
+    return PW_OK;
+  };
+  DebugOut dv, dt, dq;
+  pw_status st = timed(1, L, &dv);
+  if (st != PW_OK) return st;
+  out->sample_ms[0] = dv.walk_ms;
+  out->visit_ns = dv.n_visits ? 1e6 * dv.walk_ms / (double)dv.n_visits : 0.0;
+  out->sample_mode = 1;
+  if (table_bytes(g) > kMaxTableBytes) {
+    g->table_visit_gain = 0.0;  // the table cannot be built: always per-visit
+    g->tuned = 1;
+    return PW_OK;
+  }
+  out->table_available = 1;
+  if ((st = timed(2, L, &dt)) != PW_OK) return st;
+  if ((st = timed(2, L4.data(), &dq)) != PW_OK) return st;
+  out->sample_ms[1] = dt.walk_ms;
+  out->sample_ms[2] = dq.walk_ms;
+  // solve  T = P c + V w  for the two table runs (times in ns)
+  const double T2 = 1e6 * dt.walk_ms, T3 = 1e6 * dq.walk_ms;
+  const double P2 = (double)dt.n_probes, P3 = (double)dq.n_probes, V2 = (double)dt.n_visits, V3 = (double)dq.n_visits;
+  const double det = P2 * V3 - P3 * V2;
+  double c = 0.0, w = 0.0;
+  if (det != 0.0) {
+    c = (T2 * V3 - T3 * V2) / det;
+    w = (P2 * T3 - P3 * T2) / det;
+  }
+  if (det == 0.0 || c < 0.0 || w < 0.0) {  // degenerate sample: attribute the larger share alone
+    if (det != 0.0 && c < 0.0) {
+      c = 0.0;
+      w = V2 > 0.0 ? T2 / V2 : 0.0;
+    } else {
+      w = 0.0;
+      c = P2 > 0.0 ? T2 / P2 : 0.0;
+    }
+  }
+  out->table_probe_ns = c;
+  out->table_visit_ns = w;
+  g->table_probe_cost = c;
+  g->table_visit_gain = out->visit_ns - w;
+  g->tuned = 1;
+  const double Vs = (double)dv.n_visits, Ps = (double)dv.n_probes;
+  out->sample_mode = Ps * g->table_probe_cost < Vs * g->table_visit_gain ? 2 : 1;
+  return PW_OK;
+}
+
 pw_status pw_debug_batch_probe_q(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t,
                                  const double* eps, const int32_t* L, const uint64_t* seeds,
                                  const pw_params* params, double* beta_hat, int32_t* per_query_status,
@@ -989,13 +1091,7 @@ extern "C" pw_status pw_query_batch_noalloc(pw_graph* g, int64_t count, const in
                                    "static scratch (U_p and Q_R buffers); split the batch");
   float* u = (float*)(base + o_u);
   double* qbuf = (double*)(base + o_q);
-  int mode = params ? params->walk_mode : 0;
-  if (mode == 0) {
-    const double table_cost = (double)T.probes * (double)g->n;
-    const double visit_cost = 2.5 * 2.0 * ((double)T.steps + (double)T.u_slots);
-    mode = (table_bytes(g) <= kMaxTableBytes && table_cost < visit_cost) ? 2 : 1;
-  }
-  if (mode == 2 && table_bytes(g) > kMaxTableBytes) mode = 1;
+  const int mode = pick_walk_mode(g, params, T);
   wa.plans = plans;
   wa.tile_prefix = prefix;
   wa.totals = totals;

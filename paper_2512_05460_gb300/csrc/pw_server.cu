@@ -73,6 +73,7 @@ struct ServerArgs {
   unsigned long long* last_claim;  // %globaltimer of the latest job claim by any block
   uint32_t* exit_flag;             // set once the whole grid has been idle for idle_ns
   unsigned long long idle_ns;
+  double table_probe_cost, table_visit_gain;  // walk-mode cost model of the graph (snapshot at creation)
   BudgetArgs A;
 };
 
@@ -251,10 +252,10 @@ __global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(S
           __stcg(&S->plan.sigma2, M.sigma2);
           __stcg(&S->plan.qbar, M.qbar);
           __stcg(&S->plan.theta, M.theta);
-          // table when building z^(k) (n Feistel cycle-walks) is cheaper than
-          // evaluating it at every visit (about 2.5 passes per visit)
+          // table when building z^(k) is cheaper than evaluating it at every
+          // visit, by the graph's walk-mode cost model
           const double visits = 2.0 * (double)M.R * (double)(P.L + 1);
-          __stcg(&S->use_table, (A.table_words > 0 && (double)A.n < 2.5 * visits) ? 1u : 0u);
+          __stcg(&S->use_table, (A.table_words > 0 && A.table_probe_cost < A.table_visit_gain * visits) ? 1u : 0u);
           __threadfence();
           const unsigned long long pos = atomicAdd(A.dtail, 1ull);
           const uint32_t idx = (uint32_t)(pos % A.cap) + A.cap;
@@ -342,6 +343,7 @@ struct pw_server {
   cudaStream_t kstream = nullptr, cstream = nullptr;
   size_t smem = 0;
   int grid = 0;
+  double table_probe_cost = 0.0, table_visit_gain = 0.0;  // graph's walk-mode cost model at creation
   bool kernel_live = false;
   uint32_t active = 0;
   std::thread worker;
@@ -407,6 +409,8 @@ static ServerArgs server_args(pw_server* sv) {
   a.comp = sv->d_comp;
   a.stop = sv->d_stop;
   a.idle_ns = 5ull * 1000 * 1000;
+  a.table_probe_cost = sv->table_probe_cost;
+  a.table_visit_gain = sv->table_visit_gain;
   a.A = sv->ba;
   return a;
 }
@@ -448,7 +452,7 @@ static bool admit(pw_server* sv, const Request& rq) {
   if (!pilot) {
     const double visits = 2.0 * (double)P.R * (double)(P.L + 1);
     const uint32_t words = (uint32_t)((sv->smem - sizeof(float) * kServerRmax) / sizeof(uint32_t));
-    h.use_table = (words > 0 && (double)g->n < 2.5 * visits) ? 1u : 0u;
+    h.use_table = (words > 0 && sv->table_probe_cost < sv->table_visit_gain * visits) ? 1u : 0u;
   }
   sv->h_comp[slot].ticket = 0;
   cudaMemcpyAsync(sv->d_slots + slot, &h, sizeof(SlotDev), cudaMemcpyHostToDevice, sv->cstream);
@@ -553,6 +557,8 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
   pw_server* sv = new pw_server();
   sv->g = g;
   sv->ba = ba;
+  sv->table_probe_cost = g->table_probe_cost;
+  sv->table_visit_gain = g->table_visit_gain;
   sv->S = 4096;
   sv->cap = 4096;
   sv->pool_bytes = accum_bytes;

@@ -74,6 +74,17 @@ class pw_profile_stats(ctypes.Structure):
     ]
 
 
+class pw_tune_result(ctypes.Structure):
+    _fields_ = [
+        ("visit_ns", ctypes.c_double),
+        ("table_visit_ns", ctypes.c_double),
+        ("table_probe_ns", ctypes.c_double),
+        ("sample_ms", ctypes.c_double * 3),
+        ("table_available", ctypes.c_int32),
+        ("sample_mode", ctypes.c_int32),
+    ]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -115,6 +126,7 @@ SIGNATURES = {
     "pw_debug_batch_probe_q": (_i32, [_vp, _i64, P(_i64), P(_i64), P(_dbl), P(_i32), P(_u64), P(pw_params), P(_dbl),
                                       P(_i32), P(_u64), _i64, P(_i64), P(_i64), P(_dbl)]),
     "pw_profile": (_i32, [_vp, _i32, _i32, P(pw_profile_stats)]),
+    "pw_autotune": (_i32, [_vp, _i64, P(_i64), P(_i64), P(_dbl), P(_i32), P(_u64), P(pw_params), P(pw_tune_result)]),
     "pw_launch_count": (_u64, [ctypes.c_int]),
     "pw_last_error": (ctypes.c_char_p, []),
     "pw_version": (ctypes.c_char_p, []),
@@ -420,6 +432,22 @@ def pw_debug_batch_probe_q(g: int, s, t, eps, L, seeds, sel_query, sel_probe, pa
                                         _p(st, _i32), _p(KR, _u64), sq.size, _p(sq, _i64), _p(sp, _i64),
                                         _p(qs, _dbl)))
     return beta, st, KR, qs[: sq.size]
+
+
+def pw_autotune(g: int, s, t, eps, L, seeds=None, params=None) -> dict:
+    """Fit the graph's walk-kernel cost model on a sample batch (host arrays)."""
+    s = _arr(s, np.int64)
+    n = s.size
+    t = _arr(t, np.int64)
+    eps = _arr(np.broadcast_to(eps, (n,)), np.float64)
+    L = _arr(np.broadcast_to(L, (n,)), np.int32)
+    sd = None if seeds is None else _arr(seeds, np.uint64)
+    out = pw_tune_result()
+    _check(lib().pw_autotune(g, n, _p(s, _i64), _p(t, _i64), _p(eps, _dbl), _p(L, _i32),
+                             None if sd is None else _p(sd, _u64), _params(params), ctypes.byref(out)))
+    return {"visit_ns": out.visit_ns, "table_visit_ns": out.table_visit_ns, "table_probe_ns": out.table_probe_ns,
+            "sample_ms": list(out.sample_ms), "table_available": out.table_available,
+            "sample_mode": out.sample_mode}
 
 
 def pw_profile(g: int, enable: bool = True, reset: bool = False) -> dict:

@@ -60,20 +60,22 @@ def test_pure_host_entry_points(built_lib):
         assert built_lib.pw_default_seed(*args) == oracle.default_seed(*args)
 
 
-def test_params_struct_layout(built_lib, tmp_path):
-    """The binding's pw_params matches the header's layout (sizeof, offsetof)."""
+@pytest.mark.parametrize("struct", ["pw_params", "pw_profile_stats", "pw_tune_result"])
+def test_struct_layout(built_lib, tmp_path, struct):
+    """The binding's structs match the header's layout (sizeof, offsetof)."""
     import ctypes
     import subprocess
 
-    fields = [f for f, _ in built_lib.pw_params._fields_]
+    cls = getattr(built_lib, struct)
+    fields = [f for f, _ in cls._fields_]
     src = tmp_path / "layout.c"
-    body = "".join(f'  printf("%zu\\n", offsetof(pw_params, {f}));\n' for f in fields)
+    body = "".join(f'  printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "probewalk.h"\nint main(void) {\n'
-                   '  printf("%zu\\n", sizeof(pw_params));\n' + body + "  return 0;\n}\n")
+                   f'  printf("%zu\\n", sizeof({struct}));\n' + body + "  return 0;\n}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    want = [ctypes.sizeof(built_lib.pw_params)] + [getattr(built_lib.pw_params, f).offset for f in fields]
+    want = [ctypes.sizeof(cls)] + [getattr(cls, f).offset for f in fields]
     assert got == want
 
 
