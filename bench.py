@@ -61,13 +61,13 @@ WALK_KERNEL_NAME = {1: "walk_kernel (per-visit probe evaluation)", 2: "walk_tabl
 # Per-transition DRAM and L2 bytes of the walk kernel from the committed ncu
 # captures of the current kernels, scaled to a launch by its transitions:
 #   profiles/walk_table_kernel_ba1e5.md: one launch of 8 BA queries, 6.2515e9
-#     transitions, dram read+write 30.31 MB, lts__t_sectors 6.467e9;
+#     transitions, dram read+write 16.36 + 16.26 MB, lts__t_sectors 6.670e9;
 #   profiles/walk_kernel_rmat20.md: one per-visit launch of 8 R-MAT 2^20
 #     queries, 1.549856e9 transitions, dram 161.70 GB + 11.27 MB,
 #     lts__t_sectors 8.459e9.
 WALK_TRAFFIC = {
-    ("ba-1e5", 2): {"dram_per_transition": 30.31e6 / 6.2515e9,
-                    "l2_per_transition": 6.467e9 * 32 / 6.2515e9,
+    ("ba-1e5", 2): {"dram_per_transition": (16.363008e6 + 16.259584e6) / 6.25152e9,
+                    "l2_per_transition": 6669871597 * 32 / 6.25152e9,
                     "note": "ncu capture of 8 queries scaled by transitions; the DRAM bytes are the U_p writes, "
                             "most of which stay in L2 at the captured size"},
     ("rmat-20", 1): {"dram_per_transition": (161.701279e9 + 11.265792e6) / 1.549856e9,
