@@ -488,23 +488,29 @@ pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_
     dbg->n_probes = T.probes;
     dbg->n_visits = 2ull * (T.steps + T.u_slots);
     PW_CUDA_TRY(cudaEventCreate(&tw[0]));
-    PW_CUDA_TRY(cudaEventCreate(&tw[1]));
-    PW_CUDA_TRY(cudaEventRecord(tw[0], stream));
+    cudaError_t e = cudaEventCreate(&tw[1]);
+    if (e == cudaSuccess) e = cudaEventRecord(tw[0], stream);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(tw[0]);
+      if (tw[1]) cudaEventDestroy(tw[1]);
+      return cuda_error(e, "walk timing events");
+    }
   }
   if (T.tiles > 0) {
     if (mode == 2)
       st = launch_walk_table(g, stream, debug, wa, prefix + nq + 1, counters + 2);
     else
       st = launch_walk(g, stream, debug, wa);
-    if (st != PW_OK) return st;
   }
   if (tw[0]) {
-    PW_CUDA_TRY(cudaEventRecord(tw[1], stream));
-    PW_CUDA_TRY(cudaEventSynchronize(tw[1]));
-    PW_CUDA_TRY(cudaEventElapsedTime(&dbg->walk_ms, tw[0], tw[1]));
+    cudaError_t e = st == PW_OK ? cudaEventRecord(tw[1], stream) : cudaSuccess;
+    if (st == PW_OK && e == cudaSuccess) e = cudaEventSynchronize(tw[1]);
+    if (st == PW_OK && e == cudaSuccess) e = cudaEventElapsedTime(&dbg->walk_ms, tw[0], tw[1]);
     cudaEventDestroy(tw[0]);
     cudaEventDestroy(tw[1]);
+    if (st == PW_OK && e != cudaSuccess) return cuda_error(e, "walk timing events");
   }
+  if (st != PW_OK) return st;
   prof_end(g, stream, ev_walk, 0);
   if (g->prof.enabled) {
     g->prof.walk_launches += T.tiles > 0 ? 1 : 0;
