@@ -369,6 +369,78 @@ def run_eps_sweep(args, wl, world, rank, local):
     g.close()
 
 
+def run_series(args, wl, world, rank, local):
+    """The deterministic truncated series beta^(L) (Lemma 2.3) on the GPU
+    (pw_series_batch, FP64, 32 queries per pass): queries/s and the HBM
+    roofline of its sparse steps, timed with CUDA events (pw_profile), next
+    to the oracle's series on one host core."""
+    import torch
+
+    from oracle import exact
+    from paper_2512_05460_gb300 import build as pwbuild
+
+    pwbuild.build()
+    from paper_2512_05460_gb300 import probewalk as pw
+
+    torch.cuda.set_device(local)
+    host, s, t, seeds = workload_inputs(wl, rank)
+    nq = args.queries or 64
+    s, t = s[:nq], t[:nq]
+    L = wl["L"]
+    g = pw.Graph(host.row_ptr, host.col_idx, device=local)
+    for _ in range(args.warmup):
+        pw.pw_series_batch(g.handle, s[:32], t[:32], L)
+    pw.pw_profile(g.handle, enable=True, reset=True)
+    pw.pw_launch_count(reset=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        beta = pw.pw_series_batch(g.handle, s, t, L)
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    launches = pw.pw_launch_count(reset=True)
+    prof = pw.pw_profile(g.handle, enable=False, reset=True)
+    assert np.all(np.isfinite(beta))
+    dev_s = prof["series_ms"] / 1000.0
+    steps = prof["series_steps"]
+    # requested bytes per sparse step: per node its x row (h += x), h read and
+    # written, y written (4 x 256 B) and its 16-B record; per neighbour entry
+    # the neighbour's x row (256 B) and its 16-B record
+    step_bytes = host.n * (4 * 256 + 16) + host.nnz * (256 + 16)
+    achieved = steps * step_bytes / dev_s / 1e9
+    hbm_peak, peak_kind = load_peaks()
+    # the oracle's series on one core: per-step time from two run lengths, 32 columns
+    k = 1
+    t_0 = time.perf_counter()
+    exact.series_beta_many(host.row_ptr, host.col_idx, host.n, s[:32], t[:32], 0)
+    t_base = time.perf_counter() - t_0
+    while True:
+        t_0 = time.perf_counter()
+        exact.series_beta_many(host.row_ptr, host.col_idx, host.n, s[:32], t[:32], k)
+        t_k = time.perf_counter() - t_0
+        if t_k > 5.0 or k >= L:
+            break
+        k *= 2
+    per_step = max(t_k - t_base, 1e-9) / k
+    cpu_qps = 32 / (t_base + per_step * (L + 1))
+    line = {"metric": "truncated series beta^(L) (Lemma 2.3) on the GPU: queries/s", "value": nq * args.steps / dev_s,
+            "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}; {nq} uniform pairs; L={L}; "
+                                   "32 queries per pass (n x 32 FP64 rows)"},
+            "series_steps_per_s": steps / dev_s, "wall_s": wall,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                         "bytes_model": "per step n (4 x 256 B + 16 B) + nnz (256 B + 16 B) requested"},
+            "cpu_baseline": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": f"oracle series_beta_many on 32 queries: L=0 and L={k} timed, "
+                                       f"per-step time scaled to L={L}"},
+            "clocks": clocks, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
 def run_ours(args, wl, world, rank, local):
     import torch
 
@@ -573,6 +645,7 @@ def main():
     ap.add_argument("--no-server", action="store_true")
     ap.add_argument("--stabilized", action="store_true", help="L by the stabilization rule (Section 4.3)")
     ap.add_argument("--eps-sweep", action="store_true", help="runtime and error over eps (Fig. 2 protocol)")
+    ap.add_argument("--series", action="store_true", help="the GPU truncated series beta^(L) (Lemma 2.3)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -582,6 +655,8 @@ def main():
         run_reference(args, wl, world, rank)
     elif args.stabilized:
         run_stabilized(args, wl, world, rank, local)
+    elif args.series:
+        run_series(args, wl, world, rank, local)
     elif args.eps_sweep:
         run_eps_sweep(args, wl, world, rank, local)
     else:

@@ -271,6 +271,8 @@ typedef struct pw_profile_stats {
   uint64_t queries;
   int32_t walk_mode;           /* walk kernel of the last batch: 1 per-visit probe evaluation, 2 probe table */
   int32_t reserved;
+  double series_ms;            /* pw_series_batch passes (32 queries each), summed */
+  uint64_t series_steps;       /* sparse steps of those passes: L + 1 per pass */
 } pw_profile_stats;
 pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stats* out);
 

@@ -40,12 +40,12 @@ struct ProfileState {
   bool enabled = false;
   struct Span {
     cudaEvent_t a, b;
-    int kind;  // 0 main walk, 1 pilot walk, 2 finish
+    int kind;  // 0 main walk, 1 pilot walk, 2 finish, 3 series pass
   };
   std::vector<Span> spans;
   std::vector<cudaEvent_t> pool;
-  double walk_ms = 0, pilot_ms = 0, finish_ms = 0;
-  uint64_t walk_launches = 0, transitions = 0, pilot_transitions = 0, queries = 0;
+  double walk_ms = 0, pilot_ms = 0, finish_ms = 0, series_ms = 0;
+  uint64_t walk_launches = 0, transitions = 0, pilot_transitions = 0, queries = 0, series_steps = 0;
 };
 
 // Budget inputs shared by all queries of a call (resolved defaults).
@@ -100,6 +100,9 @@ struct pw_graph {
 namespace pw {
 
 pw_status set_error(pw_status st, const std::string& msg);
+// CUDA-event spans on a graph's stream, summed by pw_profile (no-ops unless enabled).
+void prof_begin(pw_graph* g, cudaStream_t stream, cudaEvent_t* a);
+void prof_end(pw_graph* g, cudaStream_t stream, cudaEvent_t a, int kind);
 pw_status cuda_error(cudaError_t err, const char* what);
 void count_launch();
 pw_status ensure_buffer(DeviceBuffer& b, size_t bytes);

@@ -325,14 +325,14 @@ static cudaEvent_t prof_event(pw_graph* g) {
   return e;
 }
 
-static void prof_begin(pw_graph* g, cudaStream_t stream, cudaEvent_t* a) {
+void prof_begin(pw_graph* g, cudaStream_t stream, cudaEvent_t* a) {
   *a = nullptr;
   if (!g->prof.enabled) return;
   *a = prof_event(g);
   cudaEventRecord(*a, stream);
 }
 
-static void prof_end(pw_graph* g, cudaStream_t stream, cudaEvent_t a, int kind) {
+void prof_end(pw_graph* g, cudaStream_t stream, cudaEvent_t a, int kind) {
   if (!g->prof.enabled || !a) return;
   cudaEvent_t b = prof_event(g);
   cudaEventRecord(b, stream);
@@ -832,7 +832,7 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
     PW_CUDA_TRY(cudaEventSynchronize(sp.b));
     float ms = 0.f;
     PW_CUDA_TRY(cudaEventElapsedTime(&ms, sp.a, sp.b));
-    (sp.kind == 0 ? P.walk_ms : sp.kind == 1 ? P.pilot_ms : P.finish_ms) += ms;
+    (sp.kind == 0 ? P.walk_ms : sp.kind == 1 ? P.pilot_ms : sp.kind == 2 ? P.finish_ms : P.series_ms) += ms;
     P.pool.push_back(sp.a);
     P.pool.push_back(sp.b);
   }
@@ -847,10 +847,12 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
     out->queries = P.queries;
     out->walk_mode = g->last_walk_mode;
     out->reserved = 0;
+    out->series_ms = P.series_ms;
+    out->series_steps = P.series_steps;
   }
   if (reset) {
-    P.walk_ms = P.pilot_ms = P.finish_ms = 0;
-    P.walk_launches = P.transitions = P.pilot_transitions = P.queries = 0;
+    P.walk_ms = P.pilot_ms = P.finish_ms = P.series_ms = 0;
+    P.walk_launches = P.transitions = P.pilot_transitions = P.queries = P.series_steps = 0;
   }
   P.enabled = enable != 0;
   return PW_OK;

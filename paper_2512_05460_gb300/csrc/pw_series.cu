@@ -5,8 +5,11 @@
 // 32 queries per pass, one warp lane per query column.  x, y and h are n x 32
 // row-major (a node's 32 values are one 256-byte line), so gathering x over a
 // node's neighbours reads whole lines.  Iteration i adds x_i to h and forms
-// x_{i+1} = P x_i with (P x)_v = (sum_{u in N(v)} x_u) / d_v, neighbours taken
-// from the same 16-byte records the walks use.
+// x_{i+1} = P x_i with (P x)_v = (sum_{u in N(v)} x_u) * (1/d_v), neighbours taken
+// from the same 16-byte records the walks use.  Rows of at most 1024 entries
+// take one warp each and add in CSR order; longer rows (the hubs of power-law
+// graphs) are cut into 1024-entry segments whose partial sums are added in
+// segment order, so one hub does not hold up a whole step.
 #include <math.h>
 
 #include <algorithm>
@@ -19,6 +22,7 @@
 namespace pw {
 
 constexpr int kSeriesCols = 32;
+constexpr int32_t kSeriesSegEdges = 1024;  // rows with more entries are split into segments of this size
 
 __global__ void series_init_kernel(double* __restrict__ x, double* __restrict__ h, uint32_t n) {
   const size_t total = (size_t)n * kSeriesCols;
@@ -38,23 +42,89 @@ __global__ void series_seed_kernel(double* __restrict__ x, const int2* __restric
   x[(size_t)t * kSeriesCols + c] = -1.0 / (double)node[t].z;
 }
 
-// One warp per node v: h_v += x_v; y_v = (sum over neighbours of x_u) / d_v.
-__global__ void __launch_bounds__(256) series_step_kernel(const double* __restrict__ x, double* __restrict__ y,
-                                                          double* __restrict__ h, const int4* __restrict__ rec,
-                                                          const int4* __restrict__ node, uint32_t n, int last) {
+// Sum of x_u (column = lane) over the neighbour entries [e0, e1) of one row,
+// added in CSR order.  A warp loads 32 neighbour ids with one coalesced load
+// and keeps 8 row loads in flight before adding them in order.
+__device__ __forceinline__ double series_row_sum(const double* __restrict__ x, const int4* __restrict__ rec,
+                                                 int32_t e0, int32_t e1, uint32_t lane) {
+  double acc = 0.0;
+  for (int32_t b = e0; b < e1; b += 32) {
+    const int cnt = e1 - b < 32 ? e1 - b : 32;
+    const int u_l = (int)lane < cnt ? __ldg(&rec[b + (int)lane].x) : 0;
+    int j = 0;
+    for (; j + 8 <= cnt; j += 8) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int u = __shfl_sync(0xffffffffu, u_l, j + q);
+        v[q] = __ldg(x + (size_t)u * kSeriesCols + lane);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc += v[q];
+    }
+    for (; j < cnt; ++j) {
+      const int u = __shfl_sync(0xffffffffu, u_l, j);
+      acc += __ldg(x + (size_t)u * kSeriesCols + lane);
+    }
+  }
+  return acc;
+}
+
+// 1/d_v in FP64, once per call: GB300's FP64 rate is low, and a division per
+// node and column per step would cost more than the step's additions.
+__global__ void series_inv_degree_kernel(const int4* __restrict__ node, double* __restrict__ inv, uint32_t n) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    inv[v] = 1.0 / (double)__ldg(&node[v].z);
+}
+
+// Rows of degree <= kSeriesSegEdges, one warp per row (grid-stride):
+// h_v += x_v; y_v = (sum over neighbours of x_u) * (1/d_v).  Heavier rows
+// are left to the segment kernels below.
+__global__ void __launch_bounds__(256) series_light_kernel(const double* __restrict__ x, double* __restrict__ y,
+                                                           double* __restrict__ h, const int4* __restrict__ rec,
+                                                           const int4* __restrict__ node,
+                                                           const double* __restrict__ inv, uint32_t n, int last) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int4 nv = __ldg(node + v);
+    if (nv.z > kSeriesSegEdges) continue;
     const size_t row = (size_t)v * kSeriesCols + lane;
     h[row] += x[row];
     if (last) continue;
-    const int4 nv = __ldg(node + v);
+    y[row] = series_row_sum(x, rec, nv.y, nv.y + nv.z, lane) * __ldg(inv + v);
+  }
+}
+
+// One warp per segment of a heavy row: the partial sum of its entries.
+__global__ void __launch_bounds__(256) series_segment_kernel(const double* __restrict__ x,
+                                                             double* __restrict__ partial,
+                                                             const int4* __restrict__ rec,
+                                                             const int4* __restrict__ segs, int32_t nseg) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < (uint32_t)nseg; i += warps) {
+    const int4 sg = __ldg(segs + i);  // {row, e_begin, e_end, partial slot}
+    partial[(size_t)sg.w * kSeriesCols + lane] = series_row_sum(x, rec, sg.y, sg.z, lane);
+  }
+}
+
+// One warp per heavy row: h_v += x_v; y_v = (partials in segment order) * (1/d_v).
+__global__ void __launch_bounds__(256) series_heavy_finish_kernel(const double* __restrict__ x,
+                                                                  double* __restrict__ y, double* __restrict__ h,
+                                                                  const double* __restrict__ partial,
+                                                                  const int4* __restrict__ rows, int32_t nrows,
+                                                                  const double* __restrict__ inv, int last) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < (uint32_t)nrows; i += warps) {
+    const int4 hr = __ldg(rows + i);  // {row, first partial slot, partial count, -}
+    const size_t row = (size_t)hr.x * kSeriesCols + lane;
+    h[row] += x[row];
+    if (last) continue;
     double acc = 0.0;
-    for (int32_t e = nv.y; e < nv.y + nv.z; ++e) {
-      const int u = __ldg(&rec[e].x);
-      acc += x[(size_t)u * kSeriesCols + lane];
-    }
-    y[row] = acc / (double)nv.z;
+    for (int32_t p = 0; p < hr.z; ++p) acc += partial[(size_t)(hr.y + p) * kSeriesCols + lane];
+    y[row] = acc * __ldg(inv + hr.x);
   }
 }
 
@@ -100,7 +170,26 @@ extern "C" pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* 
   PW_CUDA_TRY(cudaSetDevice(g->device));
   const size_t n = (size_t)g->n;
   const size_t bytes = sizeof(double) * n * kSeriesCols;
-  DeviceBuffer xb, yb, hb, sb, ob;
+  // rows of more than kSeriesSegEdges entries: segments {row, e_begin, e_end,
+  // partial slot} and rows {row, first slot, slot count}, in CSR order
+  std::vector<int4> segs, heavy;
+  {
+    int64_t start = 0;
+    int32_t slot = 0;
+    for (int64_t v = 0; v < g->n; ++v) {
+      const int32_t d = g->deg[(size_t)v];
+      if (d > kSeriesSegEdges) {
+        const int32_t first = slot;
+        for (int64_t e = start; e < start + d; e += kSeriesSegEdges) {
+          const int64_t e1 = std::min<int64_t>(e + kSeriesSegEdges, start + d);
+          segs.push_back(make_int4((int)v, (int)e, (int)e1, slot++));
+        }
+        heavy.push_back(make_int4((int)v, first, slot - first, 0));
+      }
+      start += d;
+    }
+  }
+  DeviceBuffer xb, yb, hb, sb, ob, segb, rowb, partb, invb;
   pw_status st;
   auto release = [&]() {
     free_buffer(xb);
@@ -108,18 +197,40 @@ extern "C" pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* 
     free_buffer(hb);
     free_buffer(sb);
     free_buffer(ob);
+    free_buffer(segb);
+    free_buffer(rowb);
+    free_buffer(partb);
+    free_buffer(invb);
   };
   if ((st = ensure_buffer(xb, bytes)) != PW_OK || (st = ensure_buffer(yb, bytes)) != PW_OK ||
       (st = ensure_buffer(hb, bytes)) != PW_OK || (st = ensure_buffer(sb, sizeof(int2) * kSeriesCols)) != PW_OK ||
-      (st = ensure_buffer(ob, sizeof(double) * kSeriesCols)) != PW_OK) {
+      (st = ensure_buffer(ob, sizeof(double) * kSeriesCols)) != PW_OK ||
+      (st = ensure_buffer(invb, sizeof(double) * n)) != PW_OK ||
+      (!segs.empty() && ((st = ensure_buffer(segb, sizeof(int4) * segs.size())) != PW_OK ||
+                         (st = ensure_buffer(rowb, sizeof(int4) * heavy.size())) != PW_OK ||
+                         (st = ensure_buffer(partb, sizeof(double) * kSeriesCols * segs.size())) != PW_OK))) {
     release();
     return st;
   }
   cudaStream_t stream = g->stream;
   const int threads = 256;
-  const int grid = g->sm_count * 8;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, series_light_kernel, threads, 0) != cudaSuccess || occ < 1)
+    occ = 1;
+  const int grid = g->sm_count * occ;
+  const int32_t nseg = (int32_t)segs.size(), nheavy = (int32_t)heavy.size();
+  const int seg_grid = (int)std::min<int64_t>((int64_t)grid, ((int64_t)nseg * 32 + threads - 1) / threads);
+  const int heavy_grid = (int)std::min<int64_t>((int64_t)grid, ((int64_t)nheavy * 32 + threads - 1) / threads);
   std::vector<int2> stv(kSeriesCols);
   cudaError_t e = cudaSuccess;
+  const double* inv = (const double*)invb.ptr;
+  series_inv_degree_kernel<<<grid, threads, 0, stream>>>(g->d_node, (double*)invb.ptr, (uint32_t)n);
+  count_launch();
+  if (nseg > 0) {
+    e = cudaMemcpyAsync(segb.ptr, segs.data(), sizeof(int4) * segs.size(), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rowb.ptr, heavy.data(), sizeof(int4) * heavy.size(), cudaMemcpyHostToDevice, stream);
+  }
   // queries with the same L share a pass: group by L in input order
   std::vector<int64_t> order((size_t)count);
   for (int64_t i = 0; i < count; ++i) order[(size_t)i] = i;
@@ -138,17 +249,32 @@ extern "C" pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* 
     double* h = (double*)hb.ptr;
     e = cudaMemcpyAsync(sb.ptr, stv.data(), sizeof(int2) * ncols, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) break;
+    cudaEvent_t ev = nullptr;
+    prof_begin(g, stream, &ev);
     series_init_kernel<<<grid, threads, 0, stream>>>(x, h, (uint32_t)n);
     series_seed_kernel<<<1, kSeriesCols, 0, stream>>>(x, (const int2*)sb.ptr, g->d_node, ncols);
     count_launch();
     count_launch();
     for (int32_t i = 0; i <= Lc; ++i) {
-      series_step_kernel<<<grid, threads, 0, stream>>>(x, y, h, g->d_rec, g->d_node, (uint32_t)n, i == Lc);
+      const int last = i == Lc;
+      series_light_kernel<<<grid, threads, 0, stream>>>(x, y, h, g->d_rec, g->d_node, inv, (uint32_t)n, last);
       count_launch();
+      if (nheavy > 0) {
+        if (!last) {
+          series_segment_kernel<<<seg_grid, threads, 0, stream>>>(x, (double*)partb.ptr, g->d_rec,
+                                                                  (const int4*)segb.ptr, nseg);
+          count_launch();
+        }
+        series_heavy_finish_kernel<<<heavy_grid, threads, 0, stream>>>(x, y, h, (const double*)partb.ptr,
+                                                                       (const int4*)rowb.ptr, nheavy, inv, last);
+        count_launch();
+      }
       std::swap(x, y);
     }
     series_reduce_kernel<<<ncols, 256, 0, stream>>>(h, (uint32_t)n, ncols, (double*)ob.ptr);
     count_launch();
+    prof_end(g, stream, ev, 3);
+    if (g->prof.enabled) g->prof.series_steps += (uint64_t)Lc + 1;
     std::vector<double> res((size_t)ncols);
     e = cudaMemcpyAsync(res.data(), ob.ptr, sizeof(double) * ncols, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);

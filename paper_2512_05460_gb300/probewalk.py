@@ -71,6 +71,8 @@ class pw_profile_stats(ctypes.Structure):
         ("queries", ctypes.c_uint64),
         ("walk_mode", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("series_ms", ctypes.c_double),
+        ("series_steps", ctypes.c_uint64),
     ]
 
 

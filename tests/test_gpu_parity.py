@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 from oracle import exact
-from pw_inputs import (barabasi_albert, complete_graph, cycle_graph, er_cycle, eps_uniform, path_graph,
+from pw_inputs import (barabasi_albert, complete_graph, cycle_graph, er_cycle, eps_uniform, from_edges, path_graph,
                        query_seeds, uniform_pairs)
 
 pytestmark = pytest.mark.gpu
@@ -351,3 +351,29 @@ def test_series_matches_oracle(pw, oracle_lib, tiny, ba):
             np.testing.assert_allclose(got[m], want, rtol=1e-9, atol=0)
     host, g = tiny
     assert pw.pw_series_batch(g.handle, [3], [3], [10])[0] == 0.0
+
+
+def test_series_hub_rows_split(pw):
+    """Rows of more than 1024 entries are summed in 1024-entry segments: a
+    cycle of 3000 nodes with chords plus a hub of degree 2500 (three
+    segments) against the oracle's series; two calls agree bit for bit."""
+    n = 3000
+    rng = np.random.default_rng(340)
+    ring = np.arange(n)
+    chords = rng.integers(0, n, size=(4000, 2))
+    hub_nb = rng.choice(np.arange(1, n), size=2500, replace=False)
+    u = np.concatenate([ring, chords[:, 0], np.zeros(2500, np.int64)])
+    v = np.concatenate([(ring + 1) % n, chords[:, 1], hub_nb])
+    host = from_edges(n, u, v, name="hub3000")
+    assert int(np.diff(host.row_ptr).max()) > 2048
+    g = pw.Graph(host.row_ptr, host.col_idx)
+    s, t = uniform_pairs(host.n, 36, 341)
+    s[:4] = 0  # queries from the hub itself
+    L = np.array([0, 1, 7, 40] * 9, np.int32)
+    got = pw.pw_series_batch(g.handle, s, t, L)
+    assert np.array_equal(got, pw.pw_series_batch(g.handle, s, t, L))
+    for Lv in (0, 1, 7, 40):
+        m = L == Lv
+        want = exact.series_beta_many(host.row_ptr, host.col_idx, host.n, s[m], t[m], int(Lv))
+        np.testing.assert_allclose(got[m], want, rtol=1e-9, atol=0)
+    g.close()
