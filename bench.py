@@ -410,6 +410,12 @@ def run_series(args, wl, world, rank, local):
     step_bytes = host.n * (4 * 256 + 16) + host.nnz * (256 + 16)
     achieved = steps * step_bytes / dev_s / 1e9
     hbm_peak, peak_kind = load_peaks()
+    # FP64 lane operations per sparse step: one addition per neighbour entry and
+    # column, one addition (h += x) and one multiplication (by 1/d_v) per node
+    # and column.  GB300's FP64 pipe: nominal 1.25 TFLOP/s counting a fused
+    # multiply-add as two, i.e. 0.625e12 lane operations/s.
+    fp64_ops = steps * 32 * (host.nnz + 2 * host.n)
+    fp64_peak = 625.0
     # the oracle's series on one core: per-step time from two run lengths, 32 columns
     k = 1
     t_0 = time.perf_counter()
@@ -430,9 +436,14 @@ def run_series(args, wl, world, rank, local):
             "config": {"workload": f"{args.workload}: {wl['desc']}; {nq} uniform pairs; L={L}; "
                                    "32 queries per pass (n x 32 FP64 rows)"},
             "series_steps_per_s": steps / dev_s, "wall_s": wall,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-                         "bytes_model": "per step n (4 x 256 B + 16 B) + nnz (256 B + 16 B) requested"},
+            "roofline": {"bound": "alu", "achieved": fp64_ops / dev_s / 1e9, "peak": fp64_peak,
+                         "unit": "G FP64 lane-ops/s", "frac": fp64_ops / dev_s / 1e9 / fp64_peak,
+                         "peak_kind": "nominal GB300 FP64 rate (1.25 TFLOP/s, FMA = 2), per lane operation",
+                         "ops_model": "per step 32 (nnz + 2 n): an addition per neighbour entry, an addition and "
+                                      "a multiplication per node, per column",
+                         "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                                 "bytes_model": "per step n (4 x 256 B + 16 B) + nnz (256 B + 16 B) requested"}},
             "cpu_baseline": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
                              "sample": f"oracle series_beta_many on 32 queries: L=0 and L={k} timed, "
                                        f"per-step time scaled to L={L}"},
