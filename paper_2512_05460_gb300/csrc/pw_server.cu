@@ -557,8 +557,11 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
   pw_server* sv = new pw_server();
   sv->g = g;
   sv->ba = ba;
-  sv->table_probe_cost = g->table_probe_cost;
-  sv->table_visit_gain = g->table_visit_gain;
+  {
+    std::lock_guard<std::mutex> guard(g->lock);  // pw_autotune may update the costs concurrently
+    sv->table_probe_cost = g->table_probe_cost;
+    sv->table_visit_gain = g->table_visit_gain;
+  }
   sv->S = 4096;
   sv->cap = 4096;
   sv->pool_bytes = accum_bytes;
