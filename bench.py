@@ -371,9 +371,9 @@ def run_eps_sweep(args, wl, world, rank, local):
 
 def run_series(args, wl, world, rank, local):
     """The deterministic truncated series beta^(L) (Lemma 2.3) on the GPU
-    (pw_series_batch, FP64, 32 queries per pass): queries/s and the HBM
-    roofline of its sparse steps, timed with CUDA events (pw_profile), next
-    to the oracle's series on one host core."""
+    (pw_series_batch, double-float steps, 32 queries per pass): queries/s and
+    the HBM roofline of its sparse steps, timed with CUDA events (pw_profile),
+    next to the oracle's FP64 series on one host core."""
     import torch
 
     from oracle import exact
@@ -410,12 +410,8 @@ def run_series(args, wl, world, rank, local):
     step_bytes = host.n * (4 * 256 + 16) + host.nnz * (256 + 16)
     achieved = steps * step_bytes / dev_s / 1e9
     hbm_peak, peak_kind = load_peaks()
-    # FP64 lane operations per sparse step: one addition per neighbour entry and
-    # column, one addition (h += x) and one multiplication (by 1/d_v) per node
-    # and column.  GB300's FP64 pipe: nominal 1.25 TFLOP/s counting a fused
-    # multiply-add as two, i.e. 0.625e12 lane operations/s.
-    fp64_ops = steps * 32 * (host.nnz + 2 * host.n)
-    fp64_peak = 625.0
+    # the steps run in double-float (FP32 pairs, about 20 FP32 operations per
+    # addition), so they are bound by memory, not by GB300's FP64 rate
     # the oracle's series on one core: per-step time from two run lengths, 32 columns
     k = 1
     t_0 = time.perf_counter()
@@ -432,18 +428,16 @@ def run_series(args, wl, world, rank, local):
     cpu_qps = 32 / (t_base + per_step * (L + 1))
     line = {"metric": "truncated series beta^(L) (Lemma 2.3) on the GPU: queries/s", "value": nq * args.steps / dev_s,
             "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "f32x2", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {wl['desc']}; {nq} uniform pairs; L={L}; "
-                                   "32 queries per pass (n x 32 FP64 rows)"},
+                                   "32 queries per pass (n x 32 double-float rows)"},
             "series_steps_per_s": steps / dev_s, "wall_s": wall,
-            "roofline": {"bound": "alu", "achieved": fp64_ops / dev_s / 1e9, "peak": fp64_peak,
-                         "unit": "G FP64 lane-ops/s", "frac": fp64_ops / dev_s / 1e9 / fp64_peak,
-                         "peak_kind": "nominal GB300 FP64 rate (1.25 TFLOP/s, FMA = 2), per lane operation",
-                         "ops_model": "per step 32 (nnz + 2 n): an addition per neighbour entry, an addition and "
-                                      "a multiplication per node, per column",
-                         "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                                 "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-                                 "bytes_model": "per step n (4 x 256 B + 16 B) + nnz (256 B + 16 B) requested"}},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                         "bytes_model": "per step n (4 x 256 B + 16 B) + nnz (256 B + 16 B) requested; neighbour "
+                                        "rows that hit L2 count as requested bytes",
+                         "arithmetic": "double-float (hi + lo FP32 pairs, TwoSum / fused-multiply-add TwoProd); "
+                                       "beta reduced in FP64"},
             "cpu_baseline": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
                              "sample": f"oracle series_beta_many on 32 queries: L=0 and L={k} timed, "
                                        f"per-step time scaled to L={L}"},

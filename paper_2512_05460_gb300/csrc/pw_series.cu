@@ -1,15 +1,22 @@
 // Truncated series of Lemma 2.3 on the GPU: h^(L) = sum_{i=0}^{L} P^i D^{-1} b_st
-// and beta^(L) = ||h||^2 - (1^T h)^2 / n (Eq. tr-beta-exp-Liu), FP64, for
-// batches of queries (the deterministic quantity the paper's PUSH computes).
+// and beta^(L) = ||h||^2 - (1^T h)^2 / n (Eq. tr-beta-exp-Liu), for batches of
+// queries (the deterministic quantity the paper's PUSH computes).
+//
+// Arithmetic: GB300 issues FP64 at about 2 lane operations per SM per clock,
+// against 128 for FP32, and an FP64 step was bound by that pipe.  x, y and h
+// are therefore held as double-float pairs (hi + lo, two FP32 values with
+// |lo| <= ulp(hi)/2, a 48-bit significand), added and multiplied with exact
+// error-free transformations (TwoSum, and TwoProd by fused multiply-add), each
+// a handful of FP32 operations; the final reduction to beta is FP64.
 //
 // 32 queries per pass, one warp lane per query column.  x, y and h are n x 32
-// row-major (a node's 32 values are one 256-byte line), so gathering x over a
+// row-major (a node's 32 pairs are one 256-byte row), so gathering x over a
 // node's neighbours reads whole lines.  Iteration i adds x_i to h and forms
-// x_{i+1} = P x_i with (P x)_v = (sum_{u in N(v)} x_u) * (1/d_v), neighbours taken
-// from the same 16-byte records the walks use.  Rows of at most 1024 entries
-// take one warp each and add in CSR order; longer rows (the hubs of power-law
-// graphs) are cut into 1024-entry segments whose partial sums are added in
-// segment order, so one hub does not hold up a whole step.
+// x_{i+1} = P x_i with (P x)_v = (sum_{u in N(v)} x_u) * (1/d_v), neighbours
+// taken from the same 16-byte records the walks use.  Rows of at most 1024
+// entries take one warp each and add in CSR order; longer rows (the hubs of
+// power-law graphs) are cut into 1024-entry segments whose partial sums are
+// added in segment order, so one hub does not hold up a whole step.
 #include <math.h>
 
 #include <algorithm>
@@ -24,81 +31,122 @@ namespace pw {
 constexpr int kSeriesCols = 32;
 constexpr int32_t kSeriesSegEdges = 1024;  // rows with more entries are split into segments of this size
 
-__global__ void series_init_kernel(double* __restrict__ x, double* __restrict__ h, uint32_t n) {
+// ---- double-float arithmetic (value = hi + lo) -----------------------------
+// TwoSum (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Sum of two pairs; both parts by TwoSum, then renormalised (relative error
+// about 2^-46 of the result).
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float s1, e1, s2, e2;
+  two_sum(a.x, b.x, s1, e1);
+  two_sum(a.y, b.y, s2, e2);
+  e1 = __fadd_rn(e1, s2);
+  float h = __fadd_rn(s1, e1);
+  e1 = __fsub_rn(e1, __fsub_rn(h, s1));
+  e1 = __fadd_rn(e1, e2);
+  const float hi = __fadd_rn(h, e1);
+  return make_float2(hi, __fsub_rn(e1, __fsub_rn(hi, h)));
+}
+
+// Product of two pairs; TwoProd of the high parts by fused multiply-add.
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float hi = __fadd_rn(p, e);
+  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, p)));
+}
+
+__device__ __forceinline__ float2 df_from_double(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+__global__ void series_init_kernel(float2* __restrict__ x, float2* __restrict__ h, uint32_t n) {
   const size_t total = (size_t)n * kSeriesCols;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    x[i] = 0.0;
-    h[i] = 0.0;
+    x[i] = make_float2(0.f, 0.f);
+    h[i] = make_float2(0.f, 0.f);
   }
 }
 
-__global__ void series_seed_kernel(double* __restrict__ x, const int2* __restrict__ st, const int4* __restrict__ node,
+__global__ void series_seed_kernel(float2* __restrict__ x, const int2* __restrict__ st, const int4* __restrict__ node,
                                    int ncols) {
   const int c = threadIdx.x;
   if (c >= ncols) return;
   const int s = st[c].x, t = st[c].y;
   if (s == t) return;
-  x[(size_t)s * kSeriesCols + c] = 1.0 / (double)node[s].z;
-  x[(size_t)t * kSeriesCols + c] = -1.0 / (double)node[t].z;
+  x[(size_t)s * kSeriesCols + c] = df_from_double(1.0 / (double)node[s].z);
+  x[(size_t)t * kSeriesCols + c] = df_from_double(-1.0 / (double)node[t].z);
+}
+
+// 1/d_v as a pair, once per call.
+__global__ void series_inv_degree_kernel(const int4* __restrict__ node, float2* __restrict__ inv, uint32_t n) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    inv[v] = df_from_double(1.0 / (double)__ldg(&node[v].z));
 }
 
 // Sum of x_u (column = lane) over the neighbour entries [e0, e1) of one row,
 // added in CSR order.  A warp loads 32 neighbour ids with one coalesced load
 // and keeps 8 row loads in flight before adding them in order.
-__device__ __forceinline__ double series_row_sum(const double* __restrict__ x, const int4* __restrict__ rec,
+__device__ __forceinline__ float2 series_row_sum(const float2* __restrict__ x, const int4* __restrict__ rec,
                                                  int32_t e0, int32_t e1, uint32_t lane) {
-  double acc = 0.0;
+  float2 acc = make_float2(0.f, 0.f);
   for (int32_t b = e0; b < e1; b += 32) {
     const int cnt = e1 - b < 32 ? e1 - b : 32;
     const int u_l = (int)lane < cnt ? __ldg(&rec[b + (int)lane].x) : 0;
     int j = 0;
     for (; j + 8 <= cnt; j += 8) {
-      double v[8];
+      float2 v[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int u = __shfl_sync(0xffffffffu, u_l, j + q);
         v[q] = __ldg(x + (size_t)u * kSeriesCols + lane);
       }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc += v[q];
+      for (int q = 0; q < 8; ++q) acc = df_add(acc, v[q]);
     }
     for (; j < cnt; ++j) {
       const int u = __shfl_sync(0xffffffffu, u_l, j);
-      acc += __ldg(x + (size_t)u * kSeriesCols + lane);
+      acc = df_add(acc, __ldg(x + (size_t)u * kSeriesCols + lane));
     }
   }
   return acc;
 }
 
-// 1/d_v in FP64, once per call: GB300's FP64 rate is low, and a division per
-// node and column per step would cost more than the step's additions.
-__global__ void series_inv_degree_kernel(const int4* __restrict__ node, double* __restrict__ inv, uint32_t n) {
-  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-    inv[v] = 1.0 / (double)__ldg(&node[v].z);
-}
-
-// Rows of degree <= kSeriesSegEdges, one warp per row (grid-stride):
+// Rows of degree <= kSeriesSegEdges, one warp per row (grid-stride, the next
+// row's record fetched while this one is summed):
 // h_v += x_v; y_v = (sum over neighbours of x_u) * (1/d_v).  Heavier rows
 // are left to the segment kernels below.
-__global__ void __launch_bounds__(256) series_light_kernel(const double* __restrict__ x, double* __restrict__ y,
-                                                           double* __restrict__ h, const int4* __restrict__ rec,
+__global__ void __launch_bounds__(256) series_light_kernel(const float2* __restrict__ x, float2* __restrict__ y,
+                                                           float2* __restrict__ h, const int4* __restrict__ rec,
                                                            const int4* __restrict__ node,
-                                                           const double* __restrict__ inv, uint32_t n, int last) {
+                                                           const float2* __restrict__ inv, uint32_t n, int last) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-    const int4 nv = __ldg(node + v);
-    if (nv.z > kSeriesSegEdges) continue;
-    const size_t row = (size_t)v * kSeriesCols + lane;
-    h[row] += x[row];
-    if (last) continue;
-    y[row] = series_row_sum(x, rec, nv.y, nv.y + nv.z, lane) * __ldg(inv + v);
+  uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int4 nv = v < n ? __ldg(node + v) : make_int4(0, 0, 0, 0);
+  for (; v < n; v += warps) {
+    const uint32_t vn = v + warps;
+    const int4 nv_next = vn < n ? __ldg(node + vn) : make_int4(0, 0, 0, 0);  // in flight during this row
+    if (nv.z <= kSeriesSegEdges) {
+      const size_t row = (size_t)v * kSeriesCols + lane;
+      h[row] = df_add(h[row], x[row]);
+      if (!last) y[row] = df_mul(series_row_sum(x, rec, nv.y, nv.y + nv.z, lane), __ldg(inv + v));
+    }
+    nv = nv_next;
   }
 }
 
 // One warp per segment of a heavy row: the partial sum of its entries.
-__global__ void __launch_bounds__(256) series_segment_kernel(const double* __restrict__ x,
-                                                             double* __restrict__ partial,
+__global__ void __launch_bounds__(256) series_segment_kernel(const float2* __restrict__ x,
+                                                             float2* __restrict__ partial,
                                                              const int4* __restrict__ rec,
                                                              const int4* __restrict__ segs, int32_t nseg) {
   const uint32_t lane = threadIdx.x & 31u;
@@ -110,33 +158,34 @@ __global__ void __launch_bounds__(256) series_segment_kernel(const double* __res
 }
 
 // One warp per heavy row: h_v += x_v; y_v = (partials in segment order) * (1/d_v).
-__global__ void __launch_bounds__(256) series_heavy_finish_kernel(const double* __restrict__ x,
-                                                                  double* __restrict__ y, double* __restrict__ h,
-                                                                  const double* __restrict__ partial,
+__global__ void __launch_bounds__(256) series_heavy_finish_kernel(const float2* __restrict__ x,
+                                                                  float2* __restrict__ y, float2* __restrict__ h,
+                                                                  const float2* __restrict__ partial,
                                                                   const int4* __restrict__ rows, int32_t nrows,
-                                                                  const double* __restrict__ inv, int last) {
+                                                                  const float2* __restrict__ inv, int last) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < (uint32_t)nrows; i += warps) {
     const int4 hr = __ldg(rows + i);  // {row, first partial slot, partial count, -}
     const size_t row = (size_t)hr.x * kSeriesCols + lane;
-    h[row] += x[row];
+    h[row] = df_add(h[row], x[row]);
     if (last) continue;
-    double acc = 0.0;
-    for (int32_t p = 0; p < hr.z; ++p) acc += partial[(size_t)(hr.y + p) * kSeriesCols + lane];
-    y[row] = acc * __ldg(inv + hr.x);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int32_t p = 0; p < hr.z; ++p) acc = df_add(acc, partial[(size_t)(hr.y + p) * kSeriesCols + lane]);
+    y[row] = df_mul(acc, __ldg(inv + hr.x));
   }
 }
 
-// Per column: sum of h^2 and of h over nodes (fixed order: per-thread strided
-// partial sums, then a shared-memory tree), then beta = sq - tot^2 / n.
-__global__ void series_reduce_kernel(const double* __restrict__ h, uint32_t n, int ncols, double* __restrict__ out) {
+// Per column: sum of h^2 and of h over nodes in FP64 (fixed order: per-thread
+// strided partial sums, then a shared-memory tree), then beta = sq - tot^2 / n.
+__global__ void series_reduce_kernel(const float2* __restrict__ h, uint32_t n, int ncols, double* __restrict__ out) {
   __shared__ double ssq[256], stot[256];
   const int c = blockIdx.x;
   if (c >= ncols) return;
   double sq = 0.0, tot = 0.0;
   for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-    const double x = h[(size_t)v * kSeriesCols + c];
+    const float2 p = h[(size_t)v * kSeriesCols + c];
+    const double x = (double)p.x + (double)p.y;
     sq += x * x;
     tot += x;
   }
@@ -169,7 +218,7 @@ extern "C" pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* 
   std::lock_guard<std::mutex> guard(g->lock);
   PW_CUDA_TRY(cudaSetDevice(g->device));
   const size_t n = (size_t)g->n;
-  const size_t bytes = sizeof(double) * n * kSeriesCols;
+  const size_t bytes = sizeof(float2) * n * kSeriesCols;
   // rows of more than kSeriesSegEdges entries: segments {row, e_begin, e_end,
   // partial slot} and rows {row, first slot, slot count}, in CSR order
   std::vector<int4> segs, heavy;
@@ -205,10 +254,10 @@ extern "C" pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* 
   if ((st = ensure_buffer(xb, bytes)) != PW_OK || (st = ensure_buffer(yb, bytes)) != PW_OK ||
       (st = ensure_buffer(hb, bytes)) != PW_OK || (st = ensure_buffer(sb, sizeof(int2) * kSeriesCols)) != PW_OK ||
       (st = ensure_buffer(ob, sizeof(double) * kSeriesCols)) != PW_OK ||
-      (st = ensure_buffer(invb, sizeof(double) * n)) != PW_OK ||
+      (st = ensure_buffer(invb, sizeof(float2) * n)) != PW_OK ||
       (!segs.empty() && ((st = ensure_buffer(segb, sizeof(int4) * segs.size())) != PW_OK ||
                          (st = ensure_buffer(rowb, sizeof(int4) * heavy.size())) != PW_OK ||
-                         (st = ensure_buffer(partb, sizeof(double) * kSeriesCols * segs.size())) != PW_OK))) {
+                         (st = ensure_buffer(partb, sizeof(float2) * kSeriesCols * segs.size())) != PW_OK))) {
     release();
     return st;
   }
@@ -223,8 +272,8 @@ extern "C" pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* 
   const int heavy_grid = (int)std::min<int64_t>((int64_t)grid, ((int64_t)nheavy * 32 + threads - 1) / threads);
   std::vector<int2> stv(kSeriesCols);
   cudaError_t e = cudaSuccess;
-  const double* inv = (const double*)invb.ptr;
-  series_inv_degree_kernel<<<grid, threads, 0, stream>>>(g->d_node, (double*)invb.ptr, (uint32_t)n);
+  const float2* inv = (const float2*)invb.ptr;
+  series_inv_degree_kernel<<<grid, threads, 0, stream>>>(g->d_node, (float2*)invb.ptr, (uint32_t)n);
   count_launch();
   if (nseg > 0) {
     e = cudaMemcpyAsync(segb.ptr, segs.data(), sizeof(int4) * segs.size(), cudaMemcpyHostToDevice, stream);
@@ -244,9 +293,9 @@ extern "C" pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* 
       stv[(size_t)ncols++] = make_int2((int)s[i], (int)t[i]);
       idx.push_back(i);
     }
-    double* x = (double*)xb.ptr;
-    double* y = (double*)yb.ptr;
-    double* h = (double*)hb.ptr;
+    float2* x = (float2*)xb.ptr;
+    float2* y = (float2*)yb.ptr;
+    float2* h = (float2*)hb.ptr;
     e = cudaMemcpyAsync(sb.ptr, stv.data(), sizeof(int2) * ncols, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) break;
     cudaEvent_t ev = nullptr;
@@ -261,11 +310,11 @@ extern "C" pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* 
       count_launch();
       if (nheavy > 0) {
         if (!last) {
-          series_segment_kernel<<<seg_grid, threads, 0, stream>>>(x, (double*)partb.ptr, g->d_rec,
+          series_segment_kernel<<<seg_grid, threads, 0, stream>>>(x, (float2*)partb.ptr, g->d_rec,
                                                                   (const int4*)segb.ptr, nseg);
           count_launch();
         }
-        series_heavy_finish_kernel<<<heavy_grid, threads, 0, stream>>>(x, y, h, (const double*)partb.ptr,
+        series_heavy_finish_kernel<<<heavy_grid, threads, 0, stream>>>(x, y, h, (const float2*)partb.ptr,
                                                                        (const int4*)rowb.ptr, nheavy, inv, last);
         count_launch();
       }

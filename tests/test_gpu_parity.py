@@ -339,8 +339,9 @@ def test_stabilized_ba(pw, oracle_lib, ba):
 
 
 def test_series_matches_oracle(pw, oracle_lib, tiny, ba):
-    """pw_series_batch against the oracle's series (Lemma 2.3); FP64 sums in a
-    different order, so within 1e-9 relative (n u ~ 1e-11 for n = 1e5)."""
+    """pw_series_batch against the oracle's FP64 series (Lemma 2.3).  The GPU
+    steps run in double-float (48-bit significand) and sum in a different
+    order, so the bar is 1e-9 relative."""
     for host, g in (tiny, ba):
         s, t = uniform_pairs(host.n, 40, 330)
         L = np.array([0, 1, 5, 32] * 10, np.int32)
