@@ -292,9 +292,10 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
  *   per-visit:  t = visits * visit_ns
  *   table:      t = probes * table_probe_ns + visits * table_visit_ns
  * (visits = 2 K R (L+1) summed over the batch) and stores the costs in the
- * graph: from then on walk_mode 0 (auto) in pw_query*, and servers created
- * afterwards, use the table when probes * table_probe_ns < visits *
- * (visit_ns - table_visit_ns).  Costs are whole-GPU nanoseconds, so the sample
+ * graph: from then on walk_mode 0 (auto) in pw_query* uses the table when
+ * probes * table_probe_ns < visits * (visit_ns - table_visit_ns).  Servers
+ * keep the default model (their kernels differ from the batch kernels timed
+ * here).  Costs are whole-GPU nanoseconds, so the sample
  * should fill the GPU (a few thousand probes).  When the graph's table does not
  * fit in shared memory (one bit per node in at most 200 KB: n > 1,638,336) only
  * the per-visit run is made and

@@ -73,7 +73,7 @@ struct ServerArgs {
   unsigned long long* last_claim;  // %globaltimer of the latest job claim by any block
   uint32_t* exit_flag;             // set once the whole grid has been idle for idle_ns
   unsigned long long idle_ns;
-  double table_probe_cost, table_visit_gain;  // walk-mode cost model of the graph (snapshot at creation)
+  double table_probe_cost, table_visit_gain;  // walk-mode cost model (the default one, see pw_server_create)
   BudgetArgs A;
 };
 
@@ -343,7 +343,7 @@ struct pw_server {
   cudaStream_t kstream = nullptr, cstream = nullptr;
   size_t smem = 0;
   int grid = 0;
-  double table_probe_cost = 0.0, table_visit_gain = 0.0;  // graph's walk-mode cost model at creation
+  double table_probe_cost = 0.0, table_visit_gain = 0.0;  // walk-mode cost model (default constants)
   bool kernel_live = false;
   uint32_t active = 0;
   std::thread worker;
@@ -557,11 +557,13 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
   pw_server* sv = new pw_server();
   sv->g = g;
   sv->ba = ba;
-  {
-    std::lock_guard<std::mutex> guard(g->lock);  // pw_autotune may update the costs concurrently
-    sv->table_probe_cost = g->table_probe_cost;
-    sv->table_visit_gain = g->table_visit_gain;
-  }
+  // The default walk-mode model (n Feistel passes per table against 2.5 per
+  // visit), not the graph's autotuned costs: those are fitted on the batch
+  // kernels, and the server's per-visit path runs inside the table-capable
+  // server kernel at its 64-register cap, so it is slower than walk_kernel and
+  // the batch costs would under-use the table (R-MAT 2^20: 29 vs 37 queries/s).
+  sv->table_probe_cost = (double)g->n;
+  sv->table_visit_gain = 2.5;
   sv->S = 4096;
   sv->cap = 4096;
   sv->pool_bytes = accum_bytes;
