@@ -13,7 +13,7 @@ from . import test_oracle_probe as probe_pins
 from . import test_oracle_walker as walker_pins
 
 MUTANTS = {
-    # survey reading of four Feistel rounds: non-uniform matching (Lemma 3.2)
+    # four Feistel rounds (too few for a uniform matching, Lemma 3.2)
     "four_feistel_rounds": ("P->rounds = (b <= 4) ? 12u : 8u;", "P->rounds = 4u;"),
     # X_0 term dropped from a (Algorithm 1 initialises a with z_{X_0}/d_{X_0})
     "drop_x0_term": ("float a = (float)probe_entry(P, (uint64_t)x) / dx;", "float a = 0.0f;"),
