@@ -9,7 +9,7 @@ the same batch through the host-array entry point (pw_query_batch), pinned
 staging, host-to-device and device-to-host copies included.  L2 is flushed
 (256 MiB write) between timed steps, outside the timed events.
 
---impl reference times the CPU oracle (the plain serial walker) on the box's
+--impl reference times the CPU oracle (the plain serial walker) on the machine's
 host cores on a bounded sample of the same workload.
 """
 

@@ -3,7 +3,7 @@
 Integer work is compared bit for bit (Philox words, probe vectors, walk
 trajectories, visit counts).  Floating point: U_p (FP32, fixed step order)
 is bit-exact; Q_R and beta_hat use FP64 sums in the oracle's order, so they
-are bit-exact too; every comparison also states the benchmark spec's tolerance of
+are bit-exact too; every comparison also states the required tolerance of
 1e-5 relative, which is the bar."""
 
 import math
