@@ -18,6 +18,7 @@
 // power-law graphs) are cut into 1024-entry segments whose partial sums are
 // added in segment order, so one hub does not hold up a whole step.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <string>
@@ -76,11 +77,19 @@ __global__ void series_init_kernel(float2* __restrict__ x, float2* __restrict__ 
   }
 }
 
-__global__ void series_seed_kernel(float2* __restrict__ x, const int2* __restrict__ st, const int4* __restrict__ node,
-                                   int ncols) {
+// Per-pass control block, written by the host before each pass (so one
+// captured graph serves every pass of the same L).
+struct SeriesCtl {
+  int2 st[kSeriesCols];  // (s, t) of each column
+  int32_t ncols;
+  int32_t pad;
+};
+
+__global__ void series_seed_kernel(float2* __restrict__ x, const SeriesCtl* __restrict__ ctl,
+                                   const int4* __restrict__ node) {
   const int c = threadIdx.x;
-  if (c >= ncols) return;
-  const int s = st[c].x, t = st[c].y;
+  if (c >= ctl->ncols) return;
+  const int s = ctl->st[c].x, t = ctl->st[c].y;
   if (s == t) return;
   x[(size_t)s * kSeriesCols + c] = df_from_double(1.0 / (double)node[s].z);
   x[(size_t)t * kSeriesCols + c] = df_from_double(-1.0 / (double)node[t].z);
@@ -178,10 +187,11 @@ __global__ void __launch_bounds__(256) series_heavy_finish_kernel(const float2* 
 
 // Per column: sum of h^2 and of h over nodes in FP64 (fixed order: per-thread
 // strided partial sums, then a shared-memory tree), then beta = sq - tot^2 / n.
-__global__ void series_reduce_kernel(const float2* __restrict__ h, uint32_t n, int ncols, double* __restrict__ out) {
+__global__ void series_reduce_kernel(const float2* __restrict__ h, uint32_t n, const SeriesCtl* __restrict__ ctl,
+                                     double* __restrict__ out) {
   __shared__ double ssq[256], stot[256];
   const int c = blockIdx.x;
-  if (c >= ncols) return;
+  if (c >= ctl->ncols) return;
   double sq = 0.0, tot = 0.0;
   for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
     const float2 p = h[(size_t)v * kSeriesCols + c];
@@ -252,7 +262,7 @@ extern "C" pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* 
     free_buffer(invb);
   };
   if ((st = ensure_buffer(xb, bytes)) != PW_OK || (st = ensure_buffer(yb, bytes)) != PW_OK ||
-      (st = ensure_buffer(hb, bytes)) != PW_OK || (st = ensure_buffer(sb, sizeof(int2) * kSeriesCols)) != PW_OK ||
+      (st = ensure_buffer(hb, bytes)) != PW_OK || (st = ensure_buffer(sb, sizeof(SeriesCtl))) != PW_OK ||
       (st = ensure_buffer(ob, sizeof(double) * kSeriesCols)) != PW_OK ||
       (st = ensure_buffer(invb, sizeof(float2) * n)) != PW_OK ||
       (!segs.empty() && ((st = ensure_buffer(segb, sizeof(int4) * segs.size())) != PW_OK ||
@@ -270,7 +280,6 @@ extern "C" pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* 
   const int32_t nseg = (int32_t)segs.size(), nheavy = (int32_t)heavy.size();
   const int seg_grid = (int)std::min<int64_t>((int64_t)grid, ((int64_t)nseg * 32 + threads - 1) / threads);
   const int heavy_grid = (int)std::min<int64_t>((int64_t)grid, ((int64_t)nheavy * 32 + threads - 1) / threads);
-  std::vector<int2> stv(kSeriesCols);
   cudaError_t e = cudaSuccess;
   const float2* inv = (const float2*)invb.ptr;
   series_inv_degree_kernel<<<grid, threads, 0, stream>>>(g->d_node, (float2*)invb.ptr, (uint32_t)n);
@@ -280,58 +289,88 @@ extern "C" pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* 
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(rowb.ptr, heavy.data(), sizeof(int4) * heavy.size(), cudaMemcpyHostToDevice, stream);
   }
+  // One pass (init, seed, L + 1 steps, reduce) enqueued on the stream; returns
+  // the number of kernels.  A pass of L + 1 steps is one to three launches
+  // per step, so it is captured once per distinct L as a CUDA graph and the
+  // graph is replayed for every 32-query group of that L.
+  const SeriesCtl* ctl_d = (const SeriesCtl*)sb.ptr;
+  auto enqueue_pass = [&](int32_t Lc) -> int {
+    int kernels = 0;
+    float2* x = (float2*)xb.ptr;
+    float2* y = (float2*)yb.ptr;
+    float2* h = (float2*)hb.ptr;
+    series_init_kernel<<<grid, threads, 0, stream>>>(x, h, (uint32_t)n);
+    series_seed_kernel<<<1, kSeriesCols, 0, stream>>>(x, ctl_d, g->d_node);
+    kernels += 2;
+    for (int32_t i = 0; i <= Lc; ++i) {
+      const int last = i == Lc;
+      series_light_kernel<<<grid, threads, 0, stream>>>(x, y, h, g->d_rec, g->d_node, inv, (uint32_t)n, last);
+      ++kernels;
+      if (nheavy > 0) {
+        if (!last) {
+          series_segment_kernel<<<seg_grid, threads, 0, stream>>>(x, (float2*)partb.ptr, g->d_rec,
+                                                                  (const int4*)segb.ptr, nseg);
+          ++kernels;
+        }
+        series_heavy_finish_kernel<<<heavy_grid, threads, 0, stream>>>(x, y, h, (const float2*)partb.ptr,
+                                                                       (const int4*)rowb.ptr, nheavy, inv, last);
+        ++kernels;
+      }
+      std::swap(x, y);
+    }
+    series_reduce_kernel<<<kSeriesCols, 256, 0, stream>>>(h, (uint32_t)n, ctl_d, (double*)ob.ptr);
+    return kernels + 1;
+  };
+  cudaGraphExec_t exec = nullptr;
+  int32_t exec_L = -1;
+  int exec_kernels = 0;
   // queries with the same L share a pass: group by L in input order
   std::vector<int64_t> order((size_t)count);
   for (int64_t i = 0; i < count; ++i) order[(size_t)i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return L[a] < L[b]; });
   for (size_t pos = 0; pos < order.size() && e == cudaSuccess;) {
     const int32_t Lc = L[order[pos]];
-    int ncols = 0;
+    SeriesCtl ctl;
+    memset(&ctl, 0, sizeof ctl);
     std::vector<int64_t> idx;
-    while (pos < order.size() && ncols < kSeriesCols && L[order[pos]] == Lc) {
+    while (pos < order.size() && ctl.ncols < kSeriesCols && L[order[pos]] == Lc) {
       const int64_t i = order[pos++];
-      stv[(size_t)ncols++] = make_int2((int)s[i], (int)t[i]);
+      ctl.st[ctl.ncols++] = make_int2((int)s[i], (int)t[i]);
       idx.push_back(i);
     }
-    float2* x = (float2*)xb.ptr;
-    float2* y = (float2*)yb.ptr;
-    float2* h = (float2*)hb.ptr;
-    e = cudaMemcpyAsync(sb.ptr, stv.data(), sizeof(int2) * ncols, cudaMemcpyHostToDevice, stream);
+    e = cudaMemcpyAsync(sb.ptr, &ctl, sizeof ctl, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) break;
+    if (exec_L != Lc) {
+      if (exec) cudaGraphExecDestroy(exec);
+      exec = nullptr;
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) break;
+      exec_kernels = enqueue_pass(Lc);
+      const cudaError_t e_launch = cudaGetLastError();
+      e = cudaStreamEndCapture(stream, &graph);  // always ends the capture
+      if (e == cudaSuccess) e = e_launch;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) break;
+      exec_L = Lc;
+    }
     cudaEvent_t ev = nullptr;
     prof_begin(g, stream, &ev);
-    series_init_kernel<<<grid, threads, 0, stream>>>(x, h, (uint32_t)n);
-    series_seed_kernel<<<1, kSeriesCols, 0, stream>>>(x, (const int2*)sb.ptr, g->d_node, ncols);
-    count_launch();
-    count_launch();
-    for (int32_t i = 0; i <= Lc; ++i) {
-      const int last = i == Lc;
-      series_light_kernel<<<grid, threads, 0, stream>>>(x, y, h, g->d_rec, g->d_node, inv, (uint32_t)n, last);
-      count_launch();
-      if (nheavy > 0) {
-        if (!last) {
-          series_segment_kernel<<<seg_grid, threads, 0, stream>>>(x, (float2*)partb.ptr, g->d_rec,
-                                                                  (const int4*)segb.ptr, nseg);
-          count_launch();
-        }
-        series_heavy_finish_kernel<<<heavy_grid, threads, 0, stream>>>(x, y, h, (const float2*)partb.ptr,
-                                                                       (const int4*)rowb.ptr, nheavy, inv, last);
-        count_launch();
-      }
-      std::swap(x, y);
-    }
-    series_reduce_kernel<<<ncols, 256, 0, stream>>>(h, (uint32_t)n, ncols, (double*)ob.ptr);
-    count_launch();
+    e = cudaGraphLaunch(exec, stream);
+    for (int k = 0; k < exec_kernels; ++k) count_launch();
     prof_end(g, stream, ev, 3);
+    if (e != cudaSuccess) break;
     if (g->prof.enabled) g->prof.series_steps += (uint64_t)Lc + 1;
-    std::vector<double> res((size_t)ncols);
-    e = cudaMemcpyAsync(res.data(), ob.ptr, sizeof(double) * ncols, cudaMemcpyDeviceToHost, stream);
+    std::vector<double> res((size_t)ctl.ncols);
+    e = cudaMemcpyAsync(res.data(), ob.ptr, sizeof(double) * ctl.ncols, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    for (int c = 0; c < ncols && e == cudaSuccess; ++c) {
+    for (int c = 0; c < ctl.ncols && e == cudaSuccess; ++c) {
       const int64_t i = idx[(size_t)c];
       beta_L[i] = s[i] == t[i] ? 0.0 : res[(size_t)c];
     }
   }
+  if (exec) cudaGraphExecDestroy(exec);
   release();
   if (e != cudaSuccess) return cuda_error(e, "series");
   PW_CUDA_TRY(cudaGetLastError());
