@@ -181,7 +181,8 @@ uint64_t pw_level_seed(uint64_t seed, int32_t L);
  * pw_series_batch: the deterministic beta^(L)(s,t) = ||h||^2 - (1^T h)^2 / n
  * with h = sum_{i=0}^{L} P^i D^{-1} (e_s - e_t) (Eq. tr-beta-exp-Liu), the
  * quantity the paper's PUSH baseline computes, by L sparse matrix-vector
- * products on the GPU, 32 queries of equal L per pass.  The steps run in
+ * products on the GPU, 32 queries of equal L per pass (each pass a CUDA graph,
+ * captured once per distinct L in a call and replayed).  The steps run in
  * double-float arithmetic (FP32 pairs, 48-bit significand; GB300's FP64 rate
  * is a small fraction of its FP32 rate) and beta is reduced in FP64; results
  * agree with an FP64 evaluation to 1e-9 relative (tested; 3.3e-14 measured at
