@@ -95,6 +95,8 @@ pw_status pw_graph_load(int64_t n, const int64_t* row_ptr, const int32_t* col_id
 /* Same with 32-bit row offsets. */
 pw_status pw_graph_load32(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t nnz,
                           int32_t device, uint32_t flags, pw_graph** out);
+/* Releases the device copy and scratch of a loaded graph (NULL is a no-op).
+ * No call on g may be in flight; servers on g must be destroyed first. */
 void pw_graph_free(pw_graph* g);
 /* Graph facts: n, nnz (directed entries), minimum and maximum degree,
  * bipartite flag (1 when 2-colourable: the paper assumes non-bipartite,
@@ -111,20 +113,26 @@ pw_status pw_budget(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, co
                     const pw_params* params, uint64_t* B, uint64_t* G, uint64_t* K, uint64_t* R);
 
 /* Default per-query seed: Philox4x32-10 keyed by (params seed XOR bits of eps)
- * over the counter (s, t, L, 0x5EED); first two output words. */
+ * over the counter (s, t, L, 0x5EED); first two output words.  A convention of
+ * this library (the paper fixes no seeding): it makes a query's estimate
+ * depend only on its own arguments, alone or in any batch. */
 uint64_t pw_default_seed(uint64_t global_seed, int64_t s, int64_t t, double eps, int32_t L);
 
 /* ---- queries ---------------------------------------------------------------
- * pw_query: one query, one pipeline of launches (the "one query per launch"
- * form).  eps in (0,1), L >= 0, 0 <= s,t < n.  *beta_hat (host) receives the
- * estimate of beta^(L)(s,t); it may be negative for tiny distances (the
- * U-statistic is unbiased, not positive).  s == t returns exactly 0. */
+ * pw_query: Algorithm 1 for one query (Problem 1: beta(s,t) to relative error
+ * eps with probability 1 - delta), one pipeline of launches (the "one query per
+ * launch" form): budget (line 1), the K x R walk pairs and their U_p
+ * (Eq. hatphi-def), Q_R per probe (Eq. Q-Ustat) and the median of the G block
+ * means (Eq. final-estimator).  eps in (0,1), L >= 0, 0 <= s,t < n.
+ * *beta_hat (host) receives the estimate of beta^(L)(s,t); it may be negative
+ * for tiny distances (the U-statistic is unbiased, not positive).  s == t
+ * returns exactly 0. */
 pw_status pw_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
                    const pw_params* params, double* beta_hat);
 
-/* pw_query_batch: `count` independent queries (host arrays of length count;
- * seeds may be NULL for default seeds).  All walks of all queries run in one
- * persistent launch.  beta_hat and per_query_status (host) receive the
+/* pw_query_batch: Algorithm 1 for `count` independent queries (host arrays of
+ * length count; seeds may be NULL for default seeds), each with the result
+ * pw_query gives it.  All walks of all queries run in one persistent launch.  beta_hat and per_query_status (host) receive the
  * results; the return value is PW_OK when the batch ran, even if some queries
  * have a per-query error status.  count == 0 is a no-op. */
 pw_status pw_query_batch(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
@@ -174,7 +182,9 @@ pw_status pw_query_stabilized(pw_graph* g, int64_t count, const int64_t* s, cons
                               int32_t L_max, const uint64_t* seeds, const pw_params* params, double* beta_hat,
                               int32_t* L_stop, int32_t* per_query_status);
 /* Seed of level L of a stabilized query: first two words of Philox4x32-10
- * keyed by `seed` over the counter (L, 0, 0, 0x57AB). */
+ * keyed by `seed` over the counter (L, 0, 0, 0x57AB).  A convention of this
+ * library (Section 4.3 does not say how levels are seeded): levels are
+ * independent runs. */
 uint64_t pw_level_seed(uint64_t seed, int32_t L);
 
 /* ---- truncated series (Lemma 2.3) --------------------------------------------
@@ -206,11 +216,25 @@ pw_status pw_query_blocks(pw_graph* g, int64_t s, int64_t t, double eps, int32_t
 pw_status pw_block_median(const double* block_means, int64_t G, double* out);
 
 /* ---- server (continuous batching) ----------------------------------------
- * A server keeps the graph and the per-query accumulators on the device and
- * runs a persistent kernel fed by a device work queue.  Queries are admitted
- * while their accumulator memory (16 bytes per walk tile + 8 bytes per probe)
- * fits in accum_bytes; later ones wait in a host queue.  submit never blocks
- * on the GPU; poll returns PW_PENDING until the ticket is done. */
+ * Serving Algorithm 1 (the paper has no counterpart: a deployment of the same
+ * computation).  Each query's estimate equals pw_query's for the same
+ * arguments and params, alone or in any mix.  A server keeps the graph and the
+ * per-query accumulators on the device and runs a persistent kernel fed by a
+ * device work queue.  Queries are admitted while their accumulator memory
+ * (8 bytes per probe plus 16 per pilot probe) fits in accum_bytes (at least
+ * 1 MiB); later ones wait in a host queue.  Requires R <= 4096 and G <= 2048
+ * (PILOT clamps R to 4096; other budgets beyond that fail the query with
+ * PW_ERR_ARG).
+ * pw_server_create: allocates the server on g's device and starts its
+ *   scheduler thread; *out receives the handle.
+ * pw_server_submit: queues one query (arguments as pw_query; seed NULL for
+ *   the default seed) and returns its ticket in *ticket; never blocks on the
+ *   GPU.  PW_ERR_CANCELLED once destruction has begun, PW_ERR_FULL past 2^24
+ *   queued requests.
+ * pw_server_poll: PW_OK with *beta_hat when the ticket is done (the result is
+ *   then delivered and removed), PW_PENDING before, PW_ERR_ARG for an unknown
+ *   ticket or one already delivered by poll or collect; a query that failed
+ *   returns its error status (also delivering it). */
 pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_bytes, pw_server** out);
 pw_status pw_server_submit(pw_server* srv, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
                            uint64_t* ticket);
@@ -218,11 +242,14 @@ pw_status pw_server_poll(pw_server* srv, uint64_t ticket, double* beta_hat);
 /* Move up to `cap` finished results out of the server (host arrays): ticket,
  * estimate, per-query status and latency from submit to completion (ms, as
  * seen by the scheduler thread); *count receives how many were written.  A
- * collected ticket is no longer visible to pw_server_poll. */
+ * collected ticket is delivered: pw_server_poll then reports PW_ERR_ARG. */
 pw_status pw_server_collect(pw_server* srv, int64_t cap, uint64_t* tickets, double* beta_hat, int32_t* status,
                             double* latency_ms, int64_t* count);
 /* Wait up to timeout_ms for every submitted ticket; PW_ERR_TIMEOUT otherwise. */
 pw_status pw_server_drain(pw_server* srv, int64_t timeout_ms);
+/* Cancels requests still waiting for admission (their tickets get
+ * PW_ERR_CANCELLED), waits for the admitted ones to finish, stops the kernel
+ * and frees the server.  NULL is a no-op. */
 pw_status pw_server_destroy(pw_server* srv);
 
 /* ---- debug / parity (tests) -------------------------------------------------

@@ -24,6 +24,7 @@
 #include <map>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 
 #include "pw_budget.cuh"
 #include "pw_device.cuh"
@@ -350,7 +351,8 @@ struct pw_server {
   std::mutex mu;
   std::condition_variable cv;
   std::deque<pw::Request> pending;
-  std::unordered_map<uint64_t, pw::Result> results;
+  std::unordered_map<uint64_t, pw::Result> results;    // finished, not yet delivered
+  std::unordered_set<uint64_t> unfinished;              // submitted, no result yet
   std::vector<double> slot_submit_ms;
   uint64_t next_ticket = 1, submitted = 0, completed = 0;
   bool stopping = false;
@@ -427,6 +429,7 @@ static bool admit(pw_server* sv, const Request& rq) {
   if (P.status == PW_OK && (P.R > kServerRmax || P.G > kServerGmax)) P.status = PW_ERR_ARG;
   if (P.status != PW_OK || P.K == 0) {  // invalid, or s == t: answered on the host
     sv->results[rq.ticket] = {P.status == PW_OK ? 0.0 : NAN, P.status, now_ms() - rq.t_submit_ms};
+    sv->unfinished.erase(rq.ticket);
     sv->completed++;
     return true;
   }
@@ -479,6 +482,7 @@ static void collect(pw_server* sv) {
     if (c->ticket != want) continue;
     std::atomic_thread_fence(std::memory_order_acquire);
     sv->results[want] = {c->beta, c->status, now_ms() - sv->slot_submit_ms[s]};
+    sv->unfinished.erase(want);
     sv->completed++;
     pool_free(sv, sv->slot_range[s].first, sv->slot_range[s].second);
     sv->slot_ticket[s] = 0;
@@ -639,6 +643,7 @@ pw_status pw_server_submit(pw_server* sv, int64_t s, int64_t t, double eps, int3
   rq.seed = seed ? *seed : default_seed(sv->ba.global_seed, s, t, eps, L);
   rq.t_submit_ms = now_ms();
   sv->pending.push_back(rq);
+  sv->unfinished.insert(rq.ticket);
   sv->submitted++;
   *ticket = rq.ticket;
   return PW_OK;
@@ -649,7 +654,7 @@ pw_status pw_server_poll(pw_server* sv, uint64_t ticket, double* beta_hat) {
   std::lock_guard<std::mutex> lk(sv->mu);
   auto it = sv->results.find(ticket);
   if (it == sv->results.end()) {
-    if (ticket == 0 || ticket >= sv->next_ticket) return set_error(PW_ERR_ARG, "unknown ticket");
+    if (!sv->unfinished.count(ticket)) return set_error(PW_ERR_ARG, "unknown or already delivered ticket");
     if (sv->fatal != PW_OK) return set_error(sv->fatal, sv->fatal_msg);
     return PW_PENDING;
   }
@@ -698,6 +703,7 @@ pw_status pw_server_destroy(pw_server* sv) {
       sv->stopping = true;
       for (const Request& rq : sv->pending) {
         sv->results[rq.ticket] = {NAN, PW_ERR_CANCELLED, now_ms() - rq.t_submit_ms};
+        sv->unfinished.erase(rq.ticket);
         sv->completed++;
       }
       sv->pending.clear();

@@ -137,6 +137,33 @@ def test_server_collect_and_destroy_with_queue(pw, tiny):
     pw.pw_server_destroy(srv)  # queued work is cancelled, in-flight work finishes; no hang
 
 
+def test_server_ticket_delivered_once(pw, tiny):
+    """A result is delivered once, by poll or by collect; afterwards the ticket
+    is reported as unknown instead of pending forever."""
+    host, g = tiny
+    s, t, eps, L, seeds = _queries(host.n, 4, 1100)
+    srv = pw.pw_server_create(g.handle, None, 1 << 24)
+    try:
+        tks = [pw.pw_server_submit(srv, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i]))
+               for i in range(4)]
+        pw.pw_server_drain(srv, 60000)
+        st, _ = pw.pw_server_poll(srv, tks[0])
+        assert st == pw.PW_OK
+        with pytest.raises(pw.PWError) as e1:
+            pw.pw_server_poll(srv, tks[0])
+        assert e1.value.status == pw.PW_ERR_ARG
+        got, _, cst, _ = pw.pw_server_collect(srv)
+        assert sorted(got.tolist()) == sorted(tks[1:]) and np.all(cst == 0)
+        for tk in tks[1:]:
+            with pytest.raises(pw.PWError) as e2:
+                pw.pw_server_poll(srv, tk)
+            assert e2.value.status == pw.PW_ERR_ARG
+        with pytest.raises(pw.PWError):
+            pw.pw_server_poll(srv, max(tks) + 100)
+    finally:
+        pw.pw_server_destroy(srv)
+
+
 def test_server_ba_equals_batch(pw):
     host = barabasi_albert(100_000, 5, 1)
     with pw.Graph(host.row_ptr, host.col_idx) as g:
