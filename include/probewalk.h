@@ -222,7 +222,8 @@ pw_status pw_block_median(const double* block_means, int64_t G, double* out);
  * per-query accumulators on the device and runs a persistent kernel fed by a
  * device work queue.  Queries are admitted while their accumulator memory
  * (8 bytes per probe plus 16 per pilot probe) fits in accum_bytes (at least
- * 1 MiB); later ones wait in a host queue.  Requires R <= 4096 and G <= 2048
+ * 1 MiB); later ones wait in a host queue, and a query that needs more than
+ * accum_bytes alone fails with PW_ERR_NOMEM.  Requires R <= 4096 and G <= 2048
  * (PILOT clamps R to 4096; other budgets beyond that fail the query with
  * PW_ERR_ARG).
  * pw_server_create: allocates the server on g's device and starts its

@@ -436,6 +436,12 @@ static bool admit(pw_server* sv, const Request& rq) {
   if (sv->free_slots.empty()) return false;
   const bool pilot = sv->ba.mode == PW_BUDGET_PILOT;
   const size_t bytes = sizeof(double) * (size_t)P.K + (pilot ? 2 * sizeof(double) * (size_t)PP.K : 0) + 256;
+  if (((bytes + 255) & ~(size_t)255) > sv->pool_bytes) {  // could never be admitted: fail it now
+    sv->results[rq.ticket] = {NAN, PW_ERR_NOMEM, now_ms() - rq.t_submit_ms};
+    sv->unfinished.erase(rq.ticket);
+    sv->completed++;
+    return true;
+  }
   size_t off = 0;
   if (!pool_alloc(sv, bytes, &off)) return false;
   const uint32_t slot = sv->free_slots.back();

@@ -164,6 +164,24 @@ def test_server_ticket_delivered_once(pw, tiny):
         pw.pw_server_destroy(srv)
 
 
+def test_server_query_larger_than_pool_fails(pw, tiny):
+    """eps = 0.01 needs 185,000 probes (1.5 MB of accumulators), more than a
+    1 MiB pool: the query fails with PW_ERR_NOMEM instead of waiting forever,
+    and the server keeps serving."""
+    host, g = tiny
+    srv = pw.pw_server_create(g.handle, None, 1 << 20)
+    try:
+        big = pw.pw_server_submit(srv, 3, 77, 0.01, 5, 11)
+        ok = pw.pw_server_submit(srv, 3, 77, 0.3, 5, 11)
+        pw.pw_server_drain(srv, 60000)
+        with pytest.raises(pw.PWError) as e:
+            pw.pw_server_poll(srv, big)
+        assert e.value.status == pw.PW_ERR_NOMEM
+        assert pw.pw_server_poll(srv, ok)[0] == pw.PW_OK
+    finally:
+        pw.pw_server_destroy(srv)
+
+
 def test_server_ba_equals_batch(pw):
     host = barabasi_albert(100_000, 5, 1)
     with pw.Graph(host.row_ptr, host.col_idx) as g:
