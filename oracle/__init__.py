@@ -94,6 +94,11 @@ def _configure(L):
     L.orc_query_many.restype = ctypes.c_int
     L.orc_level_seed.argtypes = [ctypes.c_uint64, ctypes.c_int32]
     L.orc_level_seed.restype = ctypes.c_uint64
+    L.orc_median_of_means.argtypes = [dp, ctypes.c_uint64, ctypes.c_uint64]
+    L.orc_median_of_means.restype = ctypes.c_double
+    L.orc_pilot_u.argtypes = [i64p, i32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                              ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, fp]
+    L.orc_pilot_u.restype = ctypes.c_int
     L.orc_max_threads.argtypes = []
     L.orc_max_threads.restype = ctypes.c_int
     return L
@@ -287,6 +292,24 @@ def stabilized(g, s: int, t: int, eps: float, L_max: int, seed: int, cfg: Budget
             return cur, L, levels
         prev = cur
         L = min(2 * L, L_max)
+
+
+def median_of_means(q, B: int, G: int) -> float:
+    """Median of the G means of B contiguous values of q (Eq. final-estimator)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    if q.size < B * G:
+        raise ValueError("q holds fewer than B*G values")
+    return float(lib().orc_median_of_means(_ptr(q, ctypes.c_double), B, G))
+
+
+def pilot_u(g, s: int, t: int, L: int, seed: int, K0: int = 64, R0: int = 32) -> np.ndarray:
+    """U_p of the PILOT stage (K0 probes x R0 replicas on the pilot streams), shape (K0, R0)."""
+    rp, ci = _csr(g)
+    u = np.zeros(K0 * R0, np.float32)
+    if lib().orc_pilot_u(_ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32), g.n, s, t, L, seed, K0, R0,
+                         _ptr(u, ctypes.c_float)) != 0:
+        raise ValueError("invalid pilot arguments")
+    return u.reshape(K0, R0)
 
 
 def max_threads() -> int:

@@ -441,6 +441,20 @@ int orc_query(const int64_t* row_ptr, const int32_t* col_idx, int64_t n, int64_t
   return 0;
 }
 
+/* Median of the G block means of q[0 .. B*G) (tests pin it directly). */
+double orc_median_of_means(const double* q, uint64_t B, uint64_t G) { return median_of_means(q, B, G); }
+
+/* U_p of the PILOT stage's K0 probes x R0 replicas, probe-major (tests pin the
+ * pilot's sigma^2 and theta against these replicas). */
+int orc_pilot_u(const int64_t* row_ptr, const int32_t* col_idx, int64_t n, int64_t s, int64_t t, int32_t L,
+                uint64_t seed, int32_t K0, int32_t R0, float* u_out) {
+  if (n < 2 || s < 0 || t < 0 || s >= n || t >= n || s == t || L < 0 || K0 < 1 || R0 < 2) return -1;
+  for (int32_t k = 0; k < K0; ++k)
+    probe_q(row_ptr, col_idx, (uint64_t)n, s, t, L, seed, (uint32_t)k, (uint64_t)R0, ORC_TAG_PROBE_PILOT,
+            ORC_TAG_WALK_PILOT, u_out + (uint64_t)k * (uint64_t)R0, NULL, NULL, NULL);
+  return 0;
+}
+
 /* Budget alone (runs the pilot in PILOT mode). */
 int orc_budget_query(const int64_t* row_ptr, const int32_t* col_idx, int64_t n, int64_t s, int64_t t, double eps,
                      int32_t L, uint64_t seed, const orc_budget_cfg* cfg, uint64_t* budget_out, double* pilot_out) {

@@ -128,6 +128,32 @@ def test_debug_query_fixed_ragged_bit_exact(pw, oracle_lib, tiny, B, G, R, L, wa
     _compare_query(pw, host, g, 10, 20, 0.3, L, 424242, params, cfg)
 
 
+@pytest.mark.parametrize("walk_mode", [1, 2])
+def test_even_G_delta_005_bit_exact(pw, oracle_lib, tiny, walk_mode):
+    """delta = 0.05 gives G = 24 block means, an even count: the median is the
+    mean of the two middle ones on the device as in the oracle (pw_debug_query,
+    pw_query_batch and pw_query, element by element)."""
+    host, g = tiny
+    params = pw.make_params(delta=0.05, walk_mode=walk_mode)
+    cfg = oracle.budget_cfg(delta=0.05)
+    dev, _ = _compare_query(pw, host, g, 3, 77, 0.2, 32, 12345, params, cfg)
+    assert dev["G"] == 24
+    s, t = uniform_pairs(host.n, 16, 410)
+    seeds = query_seeds(16, 411)
+    beta, st = pw.pw_query_batch(g.handle, s, t, 0.2, 32, seeds, params)
+    ob, ob_budget, ost = oracle.query_many(host, s, t, 0.2, 32, seeds, cfg)
+    assert np.all(st == 0) and np.all(ost == 0) and np.all(ob_budget[:, 1] == 24)
+    np.testing.assert_allclose(beta, ob, rtol=REL_TOL, atol=0)
+    np.testing.assert_array_equal(beta, ob)
+    for i in range(3):
+        assert pw.pw_query(g.handle, int(s[i]), int(t[i]), 0.2, 32, int(seeds[i]), params) == ob[i]
+    # delta = 0.02 gives G = 32
+    b2, _ = pw.pw_query_batch(g.handle, s[:4], t[:4], 0.2, 32, seeds[:4], pw.make_params(delta=0.02))
+    o2, bud2, _ = oracle.query_many(host, s[:4], t[:4], 0.2, 32, seeds[:4], oracle.budget_cfg(delta=0.02))
+    assert np.all(bud2[:, 1] == 32)
+    np.testing.assert_array_equal(b2, o2)
+
+
 @pytest.mark.parametrize("mode", ["THEORY", "SCALED"])
 def test_budget_modes_match_oracle(pw, oracle_lib, tiny, mode):
     host, g = tiny

@@ -66,6 +66,21 @@ def test_server_burst_equals_batch(pw, tiny):
     np.testing.assert_array_equal(_serve(pw, g, *q), want)
 
 
+def test_server_even_G_matches_oracle(pw, oracle_lib, tiny):
+    """delta = 0.05 (G = 24, an even number of block means): the server's final
+    median equals the oracle's for every query."""
+    import oracle
+
+    host, g = tiny
+    s, t, eps, L, seeds = _queries(host.n, 16, 550)
+    params = pw.make_params(delta=0.05)
+    got = _serve(pw, g, s, t, eps, L, seeds, params=params)
+    want, budgets, st = oracle.query_many(host, s, t, eps, L, seeds, oracle.budget_cfg(delta=0.05))
+    assert np.all(st == 0) and np.all(budgets[s != t, 1] == 24)
+    np.testing.assert_allclose(got, want, rtol=1e-5, atol=0)
+    np.testing.assert_array_equal(got, want)
+
+
 def test_server_arrivals_while_busy_equal_batch(pw, tiny):
     host, g = tiny
     q = _queries(host.n, 40, 600)

@@ -169,3 +169,74 @@ def test_bipartite_grid_series_oscillates():
     even = exact.series_beta(g.row_ptr, g.col_idx, 6, 0, 1, 400)
     odd = exact.series_beta(g.row_ptr, g.col_idx, 6, 0, 1, 401)
     assert abs(even - odd) > 1e-3
+
+
+# ---------------------------------------------------------------------------
+# Effective resistance (proof of Lemma 3.5) and the mixing parameter lambda
+# (Section 2.1), pinned by closed forms and Foster's theorem.  The helpers take
+# the module so that planted mistakes in a copy of it can be run through them.
+# ---------------------------------------------------------------------------
+
+def circulant(n, steps):
+    u = np.concatenate([np.arange(n)] * len(steps))
+    v = np.concatenate([(np.arange(n) + s) % n for s in steps])
+    from pw_inputs import from_edges
+
+    return from_edges(n, u, v, name=f"circ{n}")
+
+
+def petersen():
+    from pw_inputs import from_edges
+
+    outer = [(i, (i + 1) % 5) for i in range(5)]
+    spokes = [(i, i + 5) for i in range(5)]
+    inner = [(5 + i, 5 + (i + 2) % 5) for i in range(5)]
+    e = np.array(outer + spokes + inner)
+    return from_edges(10, e[:, 0], e[:, 1], name="petersen")
+
+
+def check_effective_resistance(ex):
+    for n in (3, 5, 8):  # K_n: 2/n
+        g = complete_graph(n)
+        assert ex.effective_resistance(g.row_ptr, g.col_idx, n, 0, n - 1) == pytest.approx(2 / n, rel=1e-11)
+    for n in (2, 5, 9):  # P_n: resistors in series, |s - t|
+        g = path_graph(n)
+        for s, t in ((0, n - 1), (1, n // 2)):
+            assert ex.effective_resistance(g.row_ptr, g.col_idx, n, s, t) == pytest.approx(abs(s - t), rel=1e-10,
+                                                                                          abs=1e-12)
+    for n in (4, 7, 10):  # C_n: paths of k and n - k edges in parallel, k (n - k) / n
+        g = cycle_graph(n)
+        for k in range(1, n):
+            assert ex.effective_resistance(g.row_ptr, g.col_idx, n, 0, k) == pytest.approx(k * (n - k) / n, rel=1e-10)
+    # Foster's theorem: the effective resistances of the edges sum to n - 1
+    for g in (er_cycle(30, 0.2, 4), barabasi_albert(40, 2, 9), petersen()):
+        src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+        tot = sum(ex.effective_resistance(g.row_ptr, g.col_idx, g.n, int(a), int(b))
+                  for a, b in zip(src, g.col_idx) if a < b)
+        assert tot == pytest.approx(g.n - 1, rel=1e-10)
+
+
+def check_mixing_lambda(ex):
+    for n in (3, 5, 10):  # K_n: P = (J - I)/(n - 1), eigenvalues 1 and -1/(n - 1)
+        g = complete_graph(n)
+        assert ex.mixing_lambda(g.row_ptr, g.col_idx, n) == pytest.approx(1 / (n - 1), rel=1e-11)
+    for n in (5, 7, 9, 15):  # odd C_n: eigenvalues cos(2 pi k / n); the largest |.| for k >= 1 is cos(pi / n)
+        g = cycle_graph(n)
+        assert ex.mixing_lambda(g.row_ptr, g.col_idx, n) == pytest.approx(math.cos(math.pi / n), rel=1e-11)
+    for n in (4, 6, 10):  # even C_n is bipartite: -1 is an eigenvalue
+        g = cycle_graph(n)
+        assert ex.mixing_lambda(g.row_ptr, g.col_idx, n) == pytest.approx(1.0, rel=1e-11)
+    g = petersen()  # adjacency spectrum {3, 1, -2}: P has 1, 1/3, -2/3
+    assert ex.mixing_lambda(g.row_ptr, g.col_idx, 10) == pytest.approx(2 / 3, rel=1e-11)
+    for n in (12, 20):  # circulant C_n(1, 2): eigenvalues (cos(2 pi k/n) + cos(4 pi k/n)) / 2
+        g = circulant(n, (1, 2))
+        want = max(abs(math.cos(2 * math.pi * k / n) + math.cos(4 * math.pi * k / n)) / 2 for k in range(1, n))
+        assert ex.mixing_lambda(g.row_ptr, g.col_idx, n) == pytest.approx(want, rel=1e-11)
+
+
+def test_effective_resistance_closed_forms():
+    check_effective_resistance(exact)
+
+
+def test_mixing_lambda_closed_forms():
+    check_mixing_lambda(exact)

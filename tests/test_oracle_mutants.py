@@ -9,6 +9,7 @@ import pytest
 import oracle
 from pw_inputs import barabasi_albert, er_cycle
 
+from . import test_oracle_exact as exact_pins
 from . import test_oracle_probe as probe_pins
 from . import test_oracle_walker as walker_pins
 
@@ -27,6 +28,28 @@ MUTANTS = {
     "first_neighbour": ("return col_idx[row_ptr[v] + (int64_t)j];", "(void)j; return col_idx[row_ptr[v]];"),
     # smallest block mean instead of the median (Eq. final-estimator)
     "min_not_median": ("double med = (G % 2 == 1) ? means[G / 2]", "double med = (G % 2 == 1) ? means[0]"),
+    # even G: the upper middle block mean alone instead of the mean of the two middle ones
+    "even_G_upper_middle": ("(means[G / 2 - 1] + means[G / 2]) / 2.0", "means[G / 2]"),
+    # pilot variance normalised by R0 instead of R0 - 1 (biased sample variance)
+    "pilot_variance_biased": ("sum_var = sum_var + (S2 - S1 * S1 / R0) / (R0 - 1.0);",
+                              "sum_var = sum_var + (S2 - S1 * S1 / R0) / R0;"),
+    # theta not floored by theta_0 (the floor from the proof of Theorem 3.8)
+    "theta_unfloored": ("double theta = q_bar > theta0 ? q_bar : theta0;", "double theta = q_bar;"),
+}
+
+# Planted mistakes in a copy of oracle/exact.py, each caught by the closed forms
+# of test_oracle_exact.py.
+EXACT_MUTANTS = {
+    # lambda from the second eigenvalue only (odd cycles have |lambda_n| > lambda_2)
+    "lambda_second_only": ("return float(max(abs(ev[1]), abs(ev[-1])))", "return float(abs(ev[1]))"),
+    # lambda from the smallest eigenvalue only (circulant C_n(1,2) has lambda_2 > |lambda_n|)
+    "lambda_last_only": ("return float(max(abs(ev[1]), abs(ev[-1])))", "return float(abs(ev[-1]))"),
+    # R_eff with + instead of - on the cross term
+    "reff_cross_sign": ("return float(lp[s, s] + lp[t, t] - 2.0 * lp[s, t])",
+                        "return float(lp[s, s] + lp[t, t] + 2.0 * lp[s, t])"),
+    # R_eff without the factor 2 on the cross term
+    "reff_cross_factor": ("return float(lp[s, s] + lp[t, t] - 2.0 * lp[s, t])",
+                          "return float(lp[s, s] + lp[t, t] - lp[s, t])"),
 }
 
 
@@ -48,6 +71,14 @@ def _run_pins(g_tiny):
         ("replicas_unbiased", lambda: walker_pins.test_replicas_unbiased_for_phi(None)),
         ("L0_deterministic", lambda: walker_pins.test_L0_replicas_are_deterministic(None, g_tiny)),
         ("pilot_accuracy", lambda: walker_pins.test_pilot_accuracy_problem_1(None, g_tiny)),
+        ("median_golden", lambda: walker_pins.test_median_of_means_golden(None)),
+        ("even_G_query", lambda: walker_pins.test_even_G_query_takes_middle_pair(None, g_tiny)),
+        ("pilot_statistics", lambda: walker_pins.test_pilot_statistics_from_replicas(None, g_tiny, 3, 77, 32, 12345,
+                                                                                     0.2)),
+        ("pilot_statistics_far", lambda: walker_pins.test_pilot_statistics_from_replicas(None, g_tiny, 42, 43, 20,
+                                                                                         2**63 + 9, 0.05)),
+        ("pilot_statistics_hub", lambda: walker_pins.test_pilot_statistics_from_replicas(None, g_tiny, "hub", 0, 32,
+                                                                                         2, 0.2)),
     ]
     for name, fn in checks:
         if _pins_fail(fn):
@@ -70,3 +101,37 @@ def test_unmutated_copy_passes_fast_pins(oracle_lib, tmp_path, tiny_graph):
     so = oracle.build_variant(oracle.source_text(), str(tmp_path))
     with oracle.use_variant(so):
         assert _run_pins(tiny_graph) == []
+
+
+def _load_exact_variant(text, tmp_path, name):
+    import importlib.util
+
+    path = tmp_path / f"exact_{name}.py"
+    path.write_text(text)
+    spec = importlib.util.spec_from_file_location(f"exact_{name}", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(EXACT_MUTANTS))
+def test_planted_mistake_in_exact_is_caught(tmp_path, name):
+    from oracle import exact
+
+    old, new = EXACT_MUTANTS[name]
+    with open(exact.__file__) as f:
+        src = f.read()
+    assert src.count(old) == 1, "mutation anchor not found in exact.py"
+    mod = _load_exact_variant(src.replace(old, new), tmp_path, name)
+    failed = [fn.__name__ for fn in (exact_pins.check_effective_resistance, exact_pins.check_mixing_lambda)
+              if _pins_fail(fn, mod)]
+    assert failed, f"no pin caught the planted mistake {name}"
+
+
+def test_unmutated_exact_copy_passes(tmp_path):
+    from oracle import exact
+
+    with open(exact.__file__) as f:
+        mod = _load_exact_variant(f.read(), tmp_path, "copy")
+    exact_pins.check_effective_resistance(mod)
+    exact_pins.check_mixing_lambda(mod)

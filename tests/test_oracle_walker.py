@@ -194,3 +194,83 @@ def test_pilot_accuracy_problem_1(oracle_lib, tiny_graph):
     assert np.all(st == 0)
     rel = np.abs(beta - ex[s, t]) / ex[s, t]
     assert (rel <= 0.2).mean() >= 0.95
+
+
+def _median_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "median_of_means.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            head, vals = line.split("|")
+            B, G, res = head.split()
+            rows.append((int(B), int(G), float(res), [float(x) for x in vals.split()]))
+    return rows
+
+
+def test_median_of_means_golden(oracle_lib):
+    """Hand-evaluated medians of contiguous block means, odd and even G
+    (Eq. final-estimator; an even G takes the mean of the two middle means)."""
+    rows = _median_rows()
+    assert any(G % 2 == 0 for _, G, _, _ in rows) and any(G % 2 == 1 for _, G, _, _ in rows)
+    for B, G, res, q in rows:
+        assert oracle.median_of_means(q, B, G) == res, (B, G, q)
+
+
+def test_even_G_query_takes_middle_pair(oracle_lib, tiny_graph):
+    """A FIXED budget with G = 4: beta_hat is numpy's median of the query's own
+    four block means (mean of the two middle ones), not either middle value."""
+    cfg = oracle.budget_cfg(mode=oracle.MODE_FIXED, B=5, G=4, R=16)
+    out = oracle.query(tiny_graph, 11, 150, 0.2, 16, 4321, cfg, want_q=True)
+    means = out["q"].reshape(4, 5).mean(axis=1)
+    srt = np.sort(means)
+    assert srt[1] != srt[2]
+    assert out["beta"] == pytest.approx(float(np.median(means)), rel=1e-14, abs=1e-300)
+
+
+def test_G_for_even_deltas(oracle_lib, tiny_graph):
+    """G = ceil(8 ln(1/delta)) (Eq. G-value): 24 at delta = 0.05 (8 ln 20 = 23.97)
+    and 32 at delta = 0.02 (8 ln 50 = 31.30), both even."""
+    for delta, G in ((0.05, 24), (0.02, 32), (0.01, 37)):
+        got = oracle.budget(tiny_graph, 3, 77, 0.2, 32, 1, oracle.budget_cfg(delta=delta))
+        assert got["G"] == G and got["K"] == 13 * G
+
+
+def _hub_graph():
+    return barabasi_albert(3000, 2, 5)
+
+
+@pytest.mark.parametrize("s,t,L,seed,eps", [(3, 77, 32, 12345, 0.2), (10, 190, 8, 99, 0.1), (0, 1, 0, 5, 0.3),
+                                            (42, 43, 20, 2**63 + 9, 0.05), ("hub", 0, 32, 2, 0.2)])
+def test_pilot_statistics_from_replicas(oracle_lib, tiny_graph, s, t, L, seed, eps):
+    """PILOT's estimates from the pilot replicas themselves (Lemma 3.7's
+    sufficient condition R >= 4 sigma^2 / theta):
+      sigma2_hat = mean over pilot probes of numpy's unbiased sample variance;
+      q_bar      = mean of the probes' U-statistics, written as mean^2 - var/R0
+                   (equal to Eq. Q-Ustat by S1^2 - S2 = R(R-1) mean^2 - (R-1) var);
+      theta_hat  = max(q_bar, theta_0), theta_0 = (1/8)(1 - eps/2)(1/d_s + 1/d_t)^2;
+      R          = 4 sigma2_hat / theta_hat rounded up to whole warps of 32, in [32, 4096].
+    The "hub" case (the two largest hubs of a 3000-node BA graph) has a negative
+    pilot mean, so the theta_0 floor and the R clamp decide its budget."""
+    g = tiny_graph
+    if s == "hub":
+        g, s = _hub_graph(), 1
+    u = oracle.pilot_u(g, s, t, L, seed).astype(np.float64)
+    K0, R0 = u.shape
+    assert (K0, R0) == (64, 32)
+    mean = u.mean(axis=1)
+    var = u.var(axis=1, ddof=1)
+    sigma2 = float(var.mean())
+    q_bar = float((mean**2 - var / R0).mean())
+    scale = float((mean**2 + var / R0).mean())  # size of the terms that cancel in q
+    d = g.degrees
+    theta0 = 0.125 * (1 - eps / 2) * (1 / d[s] + 1 / d[t]) ** 2
+    got = oracle.budget(g, s, t, eps, L, seed)
+    assert got["sigma2_hat"] == pytest.approx(sigma2, rel=1e-12, abs=1e-300)
+    assert abs(got["q_bar"] - q_bar) <= 1e-12 * scale + 1e-300
+    assert got["theta_hat"] == pytest.approx(max(q_bar, theta0), rel=1e-9, abs=1e-12 * scale)
+    r = 4 * sigma2 / got["theta_hat"]
+    lo = min(4096, max(32, 32 * math.ceil(math.ceil(r * (1 - 1e-9)) / 32)))
+    hi = min(4096, max(32, 32 * math.ceil(math.ceil(r * (1 + 1e-9)) / 32)))
+    assert lo <= got["R"] <= hi
