@@ -58,13 +58,12 @@ def workload_eps(wl: dict, count: int, rank: int = 0) -> np.ndarray:
 SECTOR_BYTES = 32  # one 16-byte neighbour record per transition lives in one 32-byte sector
 L2_BYTES = 129 << 20
 WALK_KERNEL_NAME = {1: "walk_kernel (per-visit probe evaluation)", 2: "walk_table_kernel (per-probe table)"}
-# Per-transition DRAM and L2 bytes of the walk kernel from the committed ncu
-# captures of the current kernels, scaled to a launch by its transitions:
-#   profiles/walk_table_kernel_ba1e5.md: one launch of 8 BA queries, 6.2515e9
-#     transitions, dram read+write 16.36 + 16.26 MB, lts__t_sectors 6.670e9;
-#   profiles/walk_kernel_rmat20.md: one per-visit launch of 8 R-MAT 2^20
-#     queries, 1.549856e9 transitions, dram 161.70 GB + 11.27 MB,
-#     lts__t_sectors 8.459e9.
+# Per-transition DRAM and L2 bytes of the walk kernel from one ncu capture of
+# each kernel on a small case, scaled to a launch by its transitions:
+#   table kernel, one launch of 8 BA queries: 6.2515e9 transitions, dram
+#     read+write 16.36 + 16.26 MB, lts__t_sectors 6.670e9;
+#   per-visit kernel, one launch of 8 R-MAT 2^20 queries: 1.549856e9
+#     transitions, dram 161.70 GB + 11.27 MB, lts__t_sectors 8.459e9.
 WALK_TRAFFIC = {
     ("ba-1e5", 2): {"dram_per_transition": (16.363008e6 + 16.259584e6) / 6.25152e9,
                     "l2_per_transition": 6669871597 * 32 / 6.25152e9,

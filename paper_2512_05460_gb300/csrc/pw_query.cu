@@ -1100,6 +1100,7 @@ extern "C" pw_status pw_query_batch_noalloc(pw_graph* g, int64_t count, const in
   float* u = (float*)(base + o_u);
   double* qbuf = (double*)(base + o_q);
   const int mode = pick_walk_mode(g, params, T);
+  g->last_walk_mode = mode;
   wa.plans = plans;
   wa.tile_prefix = prefix;
   wa.totals = totals;

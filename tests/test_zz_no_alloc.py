@@ -33,9 +33,13 @@ def setup():
     g.close()
 
 
-def test_noalloc_matches_allocating_entry_point_twice(setup):
+@pytest.mark.parametrize("walk_mode", [1, 2])
+def test_noalloc_matches_allocating_entry_point_twice(setup, walk_mode):
+    """Both walk kernels (per-visit probe evaluation, per-probe table), each
+    with its own offsets into the shared array."""
     torch, pw, host, g, (s, t, eps, L, seeds) = setup
-    want, wst = pw.pw_query_batch(g.handle, s, t, eps, L, seeds)
+    params = pw.make_params(walk_mode=walk_mode)
+    want, wst = pw.pw_query_batch(g.handle, s, t, eps, L, seeds, params)
     assert np.all(wst == 0)
     dev = torch.device("cuda:0")
     n = s.size
@@ -44,8 +48,9 @@ def test_noalloc_matches_allocating_entry_point_twice(setup):
     for _ in range(2):  # the shared scratch keeps the previous call's contents
         beta = torch.full((n,), -1.0, dtype=torch.float64, device=dev)
         status = torch.full((n,), 99, dtype=torch.int32, device=dev)
-        pw.pw_query_batch_noalloc(g.handle, n, *d, beta, status, stream=stream)
+        pw.pw_query_batch_noalloc(g.handle, n, *d, beta, status, params, stream=stream)
         stream.synchronize()
+        assert pw.pw_profile(g.handle, enable=False, reset=False)["walk_mode"] == walk_mode
         got = beta.cpu().numpy()
         assert int(status.abs().sum()) == 0
         np.testing.assert_allclose(got, want, rtol=REL_TOL, atol=0)
