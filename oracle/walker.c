@@ -111,7 +111,8 @@ uint64_t orc_level_seed(uint64_t seed, int32_t L) {
 
 typedef struct {
   uint64_t n;
-  uint32_t half_bits;   /* Feistel half width h: domain is 2^(2h) >= n */
+  uint32_t hi_bits;     /* Feistel halves: domain 2^(hi_bits + lo_bits) >= n, */
+  uint32_t lo_bits;     /* hi_bits = lo_bits or lo_bits + 1 */
   uint32_t rounds;
   uint32_t round_key[ORC_FEISTEL_MAX_ROUNDS];
   uint64_t a, b;        /* hash parameters a_k in [1, p-1], b_k in [0, p-1] */
@@ -125,22 +126,29 @@ static uint32_t feistel_round_fn(uint32_t x, uint32_t key, uint32_t h) {
   return y >> (32u - h);
 }
 
-/* One pass of the balanced Feistel network on [2^(2h)]. */
+/* One pass of the Feistel network on [2^(hi + lo)] whose halves may differ by
+ * one bit (the generalised Feistel construction on a domain of the form
+ * [2^hi] x [2^lo], Black and Rogaway 2002): the left half has `wl` bits and
+ * the right half `wr`; a round replaces (left, right) by (right, left XOR
+ * F(right)), F giving `wl` bits, so the two widths trade places every round
+ * and are back to (hi, lo) after the even number of rounds used here. */
 static uint64_t feistel_once(const orc_probe* P, uint64_t x) {
-  uint32_t h = P->half_bits;
-  uint32_t mask = (h >= 32) ? 0xFFFFFFFFu : ((1u << h) - 1u);
-  uint32_t left = (uint32_t)(x >> h) & mask;
-  uint32_t right = (uint32_t)x & mask;
+  uint32_t wl = P->hi_bits, wr = P->lo_bits;
+  uint32_t left = (uint32_t)(x >> wr);
+  uint32_t right = (uint32_t)(x & (((uint64_t)1 << wr) - 1u));
   for (uint32_t i = 0; i < P->rounds; ++i) {
-    uint32_t f = feistel_round_fn(right, P->round_key[i], h) & mask;
+    uint32_t f = feistel_round_fn(right, P->round_key[i], wl);
     uint32_t new_right = left ^ f;
+    uint32_t w = wl;
     left = right;
     right = new_right;
+    wl = wr;
+    wr = w;
   }
-  return ((uint64_t)left << h) | right;
+  return ((uint64_t)left << wr) | right;
 }
 
-/* pi_k(i): cycle-walk the Feistel permutation of [2^(2h)] until it lands in [n]. */
+/* pi_k(i): cycle-walk the Feistel permutation of [2^(hi + lo)] until it lands in [n]. */
 uint64_t orc_probe_pi(const orc_probe* P, uint64_t i) {
   uint64_t x = i;
   do {
@@ -152,10 +160,14 @@ uint64_t orc_probe_pi(const orc_probe* P, uint64_t i) {
 static void probe_setup(orc_probe* P, uint64_t n, uint64_t seed, uint32_t k, uint32_t tag) {
   uint32_t w[4];
   P->n = n;
-  /* smallest even b >= 2 with 2^b >= n; halves of b/2 bits */
+  /* smallest b >= 2 with 2^b >= n, except that b = 3 becomes 4 (on [8] the
+   * 2+1-bit network leaves the matching visibly non-uniform for n = 5, 6);
+   * halves of ceil(b/2) (left) and floor(b/2) (right) bits */
   uint32_t b = 2;
-  while (b < 64 && ((uint64_t)1 << b) < n) b += 2;
-  P->half_bits = b / 2;
+  while (b < 62 && ((uint64_t)1 << b) < n) b += 1;
+  if (b == 3) b = 4;
+  P->hi_bits = (b + 1) / 2;
+  P->lo_bits = b / 2;
   P->rounds = (b <= 4) ? 12u : 8u;
   philox_seeded(seed, k, 0u, 0u, tag, w);
   uint64_t wa = (uint64_t)w[0] | ((uint64_t)w[1] << 32);

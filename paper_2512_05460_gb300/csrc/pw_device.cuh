@@ -116,16 +116,21 @@ __host__ __device__ __forceinline__ uint64_t level_seed(uint64_t seed, int32_t L
 struct Probe {
   uint32_t n;        // nodes
   uint32_t n_active; // n - r
-  uint32_t h;        // Feistel half width: domain 2^(2h) >= n
-  uint32_t rounds;   // 8, or 12 when 2h <= 4
+  uint32_t hi, lo;   // Feistel halves: domain 2^(hi + lo) >= n, hi = lo or lo + 1
+  uint32_t rounds;   // 8, or 12 when hi + lo <= 4
   uint32_t a, b;     // hash parameters, a in [1, p-1], b in [0, p-1]
   uint32_t key[12];  // round keys
 };
 
-__host__ __device__ __forceinline__ uint32_t feistel_half_bits(uint32_t n) {
+// Domain bits: the smallest b >= 2 with 2^b >= n, with b = 3 raised to 4 (the
+// 2+1-bit network on [8] pairs visibly non-uniformly for n = 5, 6).  Odd b
+// splits into a left half one bit wider than the right half.
+__host__ __device__ __forceinline__ void feistel_bits(uint32_t n, uint32_t& hi, uint32_t& lo) {
   uint32_t b = 2;
-  while (b < 32 && (1ull << b) < (uint64_t)n) b += 2;
-  return b / 2;
+  while (b < 31 && (1ull << b) < (uint64_t)n) ++b;
+  if (b == 3) b = 4;
+  hi = (b + 1) / 2;
+  lo = b / 2;
 }
 
 // Probe k of the query keyed by `seed` on stream tag `tag`:
@@ -135,8 +140,8 @@ __host__ __device__ __forceinline__ uint32_t feistel_half_bits(uint32_t n) {
 __host__ __device__ __forceinline__ Probe make_probe(uint32_t n, uint64_t seed, uint32_t k, uint32_t tag) {
   Probe P;
   P.n = n;
-  P.h = feistel_half_bits(n);
-  P.rounds = (2 * P.h <= 4) ? 12u : 8u;
+  feistel_bits(n, P.hi, P.lo);
+  P.rounds = (P.hi + P.lo <= 4) ? 12u : 8u;
   const Philox4 ab = philox_seeded(seed, k, 0u, 0u, tag);
   const uint64_t wa = (uint64_t)ab.x | ((uint64_t)ab.y << 32);
   const uint64_t wb = (uint64_t)ab.z | ((uint64_t)ab.w << 32);
@@ -164,25 +169,29 @@ __host__ __device__ __forceinline__ uint32_t feistel_f(uint32_t x, uint32_t key,
   return y >> (32u - h);
 }
 
+// One pass of the Feistel network on [2^hi] x [2^lo] (the generalised
+// construction for such domains, Black and Rogaway 2002): a round maps
+// (left, right) to (right, left ^ F(right)) with F as wide as the left half,
+// so the halves trade widths every round; after the even round count the left
+// half has hi bits again.
 template <int ROUNDS>
 __host__ __device__ __forceinline__ uint32_t feistel_pass(const Probe& P, uint32_t x) {
-  const uint32_t mask = (1u << P.h) - 1u;
-  uint32_t left = x >> P.h, right = x & mask;
+  uint32_t left = x >> P.lo, right = x & ((1u << P.lo) - 1u);
 #pragma unroll
   for (int i = 0; i < ROUNDS; ++i) {
-    const uint32_t f = feistel_f(right, P.key[i], P.h);
+    const uint32_t f = feistel_f(right, P.key[i], (i & 1) ? P.lo : P.hi);
     const uint32_t nr = left ^ f;
     left = right;
     right = nr;
   }
-  return (left << P.h) | right;
+  return (left << P.lo) | right;
 }
 
 __host__ __device__ __forceinline__ uint32_t feistel_once(const Probe& P, uint32_t x) {
   return P.rounds == 8u ? feistel_pass<8>(P, x) : feistel_pass<12>(P, x);
 }
 
-// pi_k(v) by cycle-walking the permutation of [2^(2h)] back into [n].
+// pi_k(v) by cycle-walking the permutation of [2^(hi + lo)] back into [n].
 __host__ __device__ __forceinline__ uint32_t probe_pi(const Probe& P, uint32_t v) {
   uint32_t x = v;
   do {

@@ -63,7 +63,7 @@ def _probes(n, m, seed):
     return z, pi, r
 
 
-@pytest.mark.parametrize("n", [5, 7, 8, 10, 17, 33])
+@pytest.mark.parametrize("n", [5, 7, 8, 10, 17, 20, 33, 100])
 def test_second_moment_lemma_3_2(oracle_lib, n):
     """E[z z^T] = I - 11^T/n within 5 standard errors per entry (|z_i z_j| <= 1)."""
     m = 60000
@@ -74,7 +74,7 @@ def test_second_moment_lemma_3_2(oracle_lib, n):
     assert np.max(np.abs(emp - h)) < 5 / math.sqrt(m)
 
 
-@pytest.mark.parametrize("n", [5, 7, 8, 10, 17, 33, 100])
+@pytest.mark.parametrize("n", [5, 6, 7, 8, 10, 17, 20, 33, 100])
 def test_pairing_is_uniform(oracle_lib, n):
     """The matching behind z is uniform: P(i, j paired) = (n - r)/(n (n - 1)) for every
     pair, averaged over r (the identity inside the proof of Lemma 3.2)."""
