@@ -99,6 +99,8 @@ def _configure(L):
     L.orc_pilot_u.argtypes = [i64p, i32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                               ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, fp]
     L.orc_pilot_u.restype = ctypes.c_int
+    L.orc_exact_sum_f32.argtypes = [fp, ctypes.c_int64, ctypes.c_int]
+    L.orc_exact_sum_f32.restype = ctypes.c_double
     L.orc_max_threads.argtypes = []
     L.orc_max_threads.restype = ctypes.c_int
     return L
@@ -292,6 +294,13 @@ def stabilized(g, s: int, t: int, eps: float, L_max: int, seed: int, cfg: Budget
             return cur, L, levels
         prev = cur
         L = min(2 * L, L_max)
+
+
+def exact_sum_f32(u, square: bool = False) -> float:
+    """The oracle's S1 (or S2 with square=True) of FP32 values: the exact sum
+    rounded once to the nearest double."""
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    return float(lib().orc_exact_sum_f32(_ptr(u, ctypes.c_float), u.size, 1 if square else 0))
 
 
 def median_of_means(q, B: int, G: int) -> float:

@@ -15,15 +15,16 @@
  *     h_k(u) = ((a_k u + b_k) mod p) mod 2, and z_i = (-1)^(h_k(pair(i)) + pi_k(i)).
  *   - Algorithm 1: for every probe k and replica p, two independent walks of
  *     length L from s and t; a and b accumulate z_X / d_X in FP32 in step order
- *     (Eq. hatphi-def); U_p = a - b; S1 = sum U_p, S2 = sum U_p^2 (FP64,
- *     sequential); Q_R = (S1^2 - S2) / (R(R-1)) (Eq. Q-Ustat); block means over
+ *     (Eq. hatphi-def); U_p = a - b; S1 = sum U_p, S2 = sum U_p^2 (exact sums
+ *     rounded once to FP64); Q_R = (S1^2 - S2) / (R(R-1)) (Eq. Q-Ustat); block means over
  *     G contiguous blocks of B probes and their median (Eq. final-estimator).
  *   - The budget of Algorithm 1's parameter line (Eqs. B-value, G-value,
  *     R-value, K-value) and the readings used where the paper leaves the
  *     experimental budget open (THEORY, SCALED, FIXED, PILOT).
  *
  * The routines are deliberately unoptimised: the Philox block is recomputed
- * for every step, z is recomputed for every visit, sums run in index order.
+ * for every step, z is recomputed for every visit, sums over probes run in
+ * index order.
  * Build with -ffp-contract=off (no fused multiply-add) and without fast-math.
  */
 #include <math.h>
@@ -261,6 +262,89 @@ static float walk_pair(const int64_t* row_ptr, const int32_t* col_idx, const orc
 }
 
 /* ---------------------------------------------------------------------------
+ * Exact sums.  Algorithm 1 defines S1 = sum_p U_p and S2 = sum_p U_p^2 over the
+ * R replicas of a probe.  The U_p are FP32 values, so U_p and U_p^2 are exact
+ * doubles; they are added without any rounding into a long fixed-point
+ * accumulator that spans every double (base-2^32 digits held in 64-bit
+ * integers, so carries wait until the end), and the total is rounded once to
+ * the nearest double, ties to even.  S1 and S2 are therefore the correctly
+ * rounded values of the exact sums, independent of the order of the replicas.
+ * ------------------------------------------------------------------------- */
+#define ORC_ACC_DIGITS 72
+#define ORC_ACC_LOW_EXP (-1152) /* weight of bit 0 of digit 0 */
+
+typedef struct {
+  int64_t d[ORC_ACC_DIGITS];
+} orc_exact_sum;
+
+static void exact_clear(orc_exact_sum* A) { memset(A, 0, sizeof *A); }
+
+static void exact_add(orc_exact_sum* A, double x) {
+  if (x == 0.0) return;
+  int e;
+  double m = frexp(fabs(x), &e);              /* |x| = m 2^e, m in [0.5, 1) */
+  uint64_t M = (uint64_t)ldexp(m, 53);        /* |x| = M 2^(e - 53), exactly */
+  int pos = e - 53 - ORC_ACC_LOW_EXP;         /* >= 26 for the smallest subnormal */
+  int q = pos / 32, r = pos % 32;
+  unsigned __int128 w = (unsigned __int128)M << r;
+  int64_t sign = x < 0 ? -1 : 1;
+  A->d[q] += sign * (int64_t)(uint32_t)w;
+  A->d[q + 1] += sign * (int64_t)(uint32_t)(w >> 32);
+  A->d[q + 2] += sign * (int64_t)(uint32_t)(w >> 64);
+}
+
+/* Bring every digit but the last into [0, 2^32), carrying upwards. */
+static void exact_carry(int64_t* d) {
+  for (int i = 0; i + 1 < ORC_ACC_DIGITS; ++i) {
+    int64_t c = d[i] >> 32; /* floor(d / 2^32) */
+    d[i] -= c * ((int64_t)1 << 32);
+    d[i + 1] += c;
+  }
+}
+
+/* The exact sum rounded to the nearest double, ties to even.  (Nonzero sums
+ * of FP32 values and of their squares are at least 2^-298 in magnitude, far
+ * from the subnormal range, so the final scaling by a power of two is exact.) */
+static double exact_round(const orc_exact_sum* A) {
+  int64_t d[ORC_ACC_DIGITS];
+  memcpy(d, A->d, sizeof d);
+  exact_carry(d);
+  int neg = d[ORC_ACC_DIGITS - 1] < 0;
+  if (neg) {
+    for (int i = 0; i < ORC_ACC_DIGITS; ++i) d[i] = -d[i];
+    exact_carry(d);
+  }
+  int top = ORC_ACC_DIGITS - 1;
+  while (top >= 0 && d[top] == 0) --top;
+  if (top < 0) return 0.0;
+  /* the three most significant digits as one integer, the rest as a sticky bit */
+  unsigned __int128 W = 0;
+  for (int i = top; i >= top - 2; --i) W = (W << 32) | (uint64_t)(i >= 0 ? d[i] : 0);
+  int sticky = 0;
+  for (int i = top - 3; i >= 0; --i) sticky |= d[i] != 0;
+  int bits = 0;
+  for (unsigned __int128 v = W; v; v >>= 1) ++bits;
+  int drop = bits - 53; /* >= 12: the top digit is nonzero */
+  unsigned __int128 mant = W >> drop;
+  unsigned __int128 rem = W - (mant << drop);
+  unsigned __int128 half = (unsigned __int128)1 << (drop - 1);
+  if (rem > half || (rem == half && (sticky || (mant & 1)))) mant += 1;
+  double v = ldexp((double)(uint64_t)mant, ORC_ACC_LOW_EXP + 32 * (top - 2) + drop);
+  return neg ? -v : v;
+}
+
+/* Tests: the exact sum of n FP32 values (square != 0: of their squares). */
+double orc_exact_sum_f32(const float* u, int64_t n, int square) {
+  orc_exact_sum A;
+  exact_clear(&A);
+  for (int64_t i = 0; i < n; ++i) {
+    double x = (double)u[i];
+    exact_add(&A, square ? x * x : x);
+  }
+  return exact_round(&A);
+}
+
+/* ---------------------------------------------------------------------------
  * Budget (Algorithm 1 line 1; Eqs. B-value, G-value, R-value, K-value).
  * ------------------------------------------------------------------------- */
 enum { ORC_PILOT = 0, ORC_THEORY = 1, ORC_SCALED = 2, ORC_FIXED = 3 };
@@ -299,20 +383,23 @@ static double r_theory_raw(double eps, int32_t L, double d_min, double ds, doubl
   return 128.0 * (double)(L + 1) * (double)(L + 1) / (d_min * d_min * (1.0 - eps / 2.0) * inv * inv);
 }
 
-/* Q_R for one probe: S1, S2 accumulate in FP64 in replica order. */
+/* Q_R for one probe: S1 and S2 are the exact sums over the replicas, rounded once. */
 static double probe_q(const int64_t* row_ptr, const int32_t* col_idx, uint64_t n, int64_t s, int64_t t,
                       int32_t L, uint64_t seed, uint32_t k, uint64_t R, uint32_t probe_tag,
                       uint32_t walk_tag, float* u_out, double* s1_out, double* s2_out, uint32_t* visits) {
   orc_probe P;
   probe_setup(&P, n, seed, k, probe_tag);
-  double S1 = 0.0, S2 = 0.0;
+  orc_exact_sum A1, A2;
+  exact_clear(&A1);
+  exact_clear(&A2);
   for (uint64_t p = 0; p < R; ++p) {
     float U = walk_pair(row_ptr, col_idx, &P, s, t, L, seed, (uint64_t)k * R + p, walk_tag, visits);
     if (u_out) u_out[p] = U;
     double u = (double)U;
-    S1 = S1 + u;
-    S2 = S2 + u * u;
+    exact_add(&A1, u);
+    exact_add(&A2, u * u); /* exact: the square of an FP32 value fits a double */
   }
+  double S1 = exact_round(&A1), S2 = exact_round(&A2);
   if (s1_out) *s1_out = S1;
   if (s2_out) *s2_out = S2;
   double Rd = (double)R;
@@ -443,7 +530,7 @@ int orc_query(const int64_t* row_ptr, const int32_t* col_idx, int64_t n, int64_t
   if (pilot_out) {
     pilot_out[0] = bud.sigma2_hat; pilot_out[1] = bud.q_bar; pilot_out[2] = bud.theta_hat;
   }
-  double* q = q_out ? q_out : (double*)malloc(sizeof(double) * bud.K);
+  double* q = q_out ? q_out : (double*)calloc(bud.K ? bud.K : 1, sizeof(double));
   for (uint64_t k = 0; k < bud.K; ++k) {
     q[k] = probe_q(row_ptr, col_idx, (uint64_t)n, s, t, L, seed, (uint32_t)k, bud.R, ORC_TAG_PROBE, ORC_TAG_WALK,
                    u_out ? u_out + k * bud.R : NULL, NULL, NULL, visits);

@@ -33,6 +33,12 @@ MUTANTS = {
     # pilot variance normalised by R0 instead of R0 - 1 (biased sample variance)
     "pilot_variance_biased": ("sum_var = sum_var + (S2 - S1 * S1 / R0) / (R0 - 1.0);",
                               "sum_var = sum_var + (S2 - S1 * S1 / R0) / R0;"),
+    # exact sums: halfway cases rounded up instead of to even
+    "sum_ties_up": ("(rem == half && (sticky || (mant & 1)))", "(rem == half)"),
+    # exact sums: bits below the kept window ignored when breaking a tie
+    "sum_no_sticky": ("(rem == half && (sticky || (mant & 1)))", "(rem == half && (mant & 1))"),
+    # S2 accumulated from |U_p| instead of U_p^2
+    "s2_not_squared": ("exact_add(&A2, u * u);", "exact_add(&A2, fabs(u));"),
     # theta not floored by theta_0 (the floor from the proof of Theorem 3.8)
     "theta_unfloored": ("double theta = q_bar > theta0 ? q_bar : theta0;", "double theta = q_bar;"),
 }
@@ -72,6 +78,7 @@ def _run_pins(g_tiny):
         ("L0_deterministic", lambda: walker_pins.test_L0_replicas_are_deterministic(None, g_tiny)),
         ("pilot_accuracy", lambda: walker_pins.test_pilot_accuracy_problem_1(None, g_tiny)),
         ("median_golden", lambda: walker_pins.test_median_of_means_golden(None)),
+        ("exact_sum_ties", lambda: walker_pins.test_exact_sum_ties_and_edges(None)),
         ("even_G_query", lambda: walker_pins.test_even_G_query_takes_middle_pair(None, g_tiny)),
         ("pilot_statistics", lambda: walker_pins.test_pilot_statistics_from_replicas(None, g_tiny, 3, 77, 32, 12345,
                                                                                      0.2)),

@@ -274,3 +274,49 @@ def test_pilot_statistics_from_replicas(oracle_lib, tiny_graph, s, t, L, seed, e
     lo = min(4096, max(32, 32 * math.ceil(math.ceil(r * (1 - 1e-9)) / 32)))
     hi = min(4096, max(32, 32 * math.ceil(math.ceil(r * (1 + 1e-9)) / 32)))
     assert lo <= got["R"] <= hi
+
+
+def _fraction_sum(vals):
+    from fractions import Fraction
+
+    return float(sum((Fraction(float(v)) for v in vals), Fraction(0)))
+
+
+def test_exact_sums_are_correctly_rounded(oracle_lib):
+    """S1 = sum U_p and S2 = sum U_p^2 are the exact sums rounded once (round to
+    nearest, ties to even): equal to math.fsum and to exact rational arithmetic
+    on FP32 values spread over 40 binades with heavy cancellation, whatever
+    their order."""
+    rng = np.random.default_rng(17)
+    for trial in range(20):
+        n = int(rng.integers(1, 3000))
+        mag = 2.0 ** rng.integers(-30, 10, size=n)
+        u = (rng.standard_normal(n) * mag).astype(np.float32)
+        if trial % 3 == 0:  # cancellation: add the negatives of most values back
+            u = np.concatenate([u, -u[: n // 2 + 1]]).astype(np.float32)
+        x = u.astype(np.float64)
+        s1, s2 = oracle.exact_sum_f32(u), oracle.exact_sum_f32(u, square=True)
+        assert s1 == math.fsum(x.tolist()) == _fraction_sum(x)
+        assert s2 == math.fsum((x * x).tolist()) == _fraction_sum(x * x)
+        perm = rng.permutation(u.size)
+        assert oracle.exact_sum_f32(u[perm]) == s1 and oracle.exact_sum_f32(u[perm], square=True) == s2
+
+
+def test_exact_sum_ties_and_edges(oracle_lib):
+    e = 2.0**-53
+    cases = [
+        ([1.0, e], 1.0),                       # exact tie, even neighbour below
+        ([1.0, 2 * e, e], 1.0 + 4 * e),        # 1 + 3e: tie, even neighbour above
+        ([1.0, e, 2.0**-80], 1.0 + 2 * e),     # just above the tie
+        ([1.0, e, e], 1.0 + 2 * e),            # no tie at all: sequential FP64 would give 1.0
+        ([e, e, 1.0], 1.0 + 2 * e),
+        ([-1.0, -e, -e], -(1.0 + 2 * e)),
+        ([3.0, -3.0], 0.0),
+        ([], 0.0),
+        ([2.0**100, 1.0, -(2.0**100)], 1.0),
+    ]
+    for vals, want in cases:
+        u = np.array(vals, np.float32)
+        assert u.astype(np.float64).tolist() == vals
+        got = oracle.exact_sum_f32(u)
+        assert got == want and math.copysign(1.0, got) == math.copysign(1.0, want), (vals, got, want)
