@@ -57,23 +57,13 @@ def workload_eps(wl: dict, count: int, rank: int = 0) -> np.ndarray:
 
 SECTOR_BYTES = 32  # one 16-byte neighbour record per transition lives in one 32-byte sector
 L2_BYTES = 129 << 20
-WALK_KERNEL_NAME = {1: "walk_kernel (per-visit probe evaluation)", 2: "walk_table_kernel (per-probe table)"}
-# Per-transition DRAM and L2 bytes of the walk kernel from one ncu capture of
-# each kernel on a small case, scaled to a launch by its transitions:
-#   table kernel, one launch of 8 BA queries: 6.2515e9 transitions, dram
-#     read+write 16.36 + 16.26 MB, lts__t_sectors 6.670e9;
-#   per-visit kernel, one launch of 8 R-MAT 2^20 queries: 1.549856e9
-#     transitions, dram 161.70 GB + 11.27 MB, lts__t_sectors 8.459e9.
-WALK_TRAFFIC = {
-    ("ba-1e5", 2): {"dram_per_transition": (16.363008e6 + 16.259584e6) / 6.25152e9,
-                    "l2_per_transition": 6669871597 * 32 / 6.25152e9,
-                    "note": "ncu capture of 8 queries scaled by transitions; the DRAM bytes are the U_p writes, "
-                            "most of which stay in L2 at the captured size"},
-    ("rmat-20", 1): {"dram_per_transition": (161.701279e9 + 11.265792e6) / 1.549856e9,
-                     "l2_per_transition": 8459373099 * 32 / 1.549856e9,
-                     "note": "ncu capture of 8 queries scaled by transitions; each 16-B record gather (one sector "
-                             "requested) costs about 3.3 sectors of DRAM reads"},
-}
+WALK_KERNEL_NAME = {1: "walk_kernel (per-visit probe evaluation)", 2: "walk_table_kernel (per-probe table)",
+                    3: "walk_table_kernel and walk_kernel (walk kernel chosen per query)"}
+# Per-transition DRAM and L2 bytes of a walk kernel from one ncu capture on a
+# small case of the same workload, scaled to a launch by its transitions
+# (filled per (workload, walk kernel) when a capture of the current kernels
+# exists; the line reports null traffic otherwise).
+WALK_TRAFFIC = {}
 
 
 def load_peaks():
@@ -445,6 +435,35 @@ def run_series(args, wl, world, rank, local):
     g.close()
 
 
+def batched_vs_plain(pw, name, device, params, reps=5):
+    """One batch of the workload's queries (pw_query_batch) against the same
+    queries one per call (pw_query), both host-array calls, host wall clock;
+    each after two untimed calls, so both run as replayed CUDA graphs."""
+    wl = WORKLOADS[name]
+    host, s, t, seeds = workload_inputs(wl, 0)
+    eps = workload_eps(wl, s.size)
+    L = np.full(s.size, wl["L"], np.int32)
+    with pw.Graph(host.row_ptr, host.col_idx, device=device) as g:
+        for _ in range(2):
+            pw.pw_query_batch(g.handle, s, t, eps, L, seeds, params)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            beta, st = pw.pw_query_batch(g.handle, s, t, eps, L, seeds, params)
+        batch_qps = reps * s.size / (time.perf_counter() - t0)
+        assert np.all(st == 0)
+        for i in range(2):
+            pw.pw_query(g.handle, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i]), params)
+        t0 = time.perf_counter()
+        for i in range(s.size):
+            b = pw.pw_query(g.handle, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i]), params)
+            assert b == beta[i]
+        plain_qps = s.size / (time.perf_counter() - t0)
+    return {"workload": f"{name}: {wl['desc']}; {s.size} uniform pairs; L={wl['L']}; eps={wl['eps']}",
+            "batch_queries_per_s": batch_qps, "plain_queries_per_s": plain_qps,
+            "batched_over_plain": batch_qps / plain_qps,
+            "timing": f"host wall clock, {reps} batches against one pass of single-query calls"}
+
+
 def run_ours(args, wl, world, rank, local):
     import torch
 
@@ -545,6 +564,22 @@ def run_ours(args, wl, world, rank, local):
         pw.pw_query(g.handle, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i]), params)
         lat.append(time.perf_counter() - t0)
     plain_qps = plain_n / sum(lat) if lat else None
+    # the same prefix as one batch through the same host-array entry point
+    same = None
+    if plain_n:
+        sp, tp, ep, Lp, dp = s[:plain_n], t[:plain_n], eps[:plain_n], L[:plain_n], seeds[:plain_n]
+        for _ in range(2):
+            pw.pw_query_batch(g.handle, sp, tp, ep, Lp, dp, params)
+        t0 = time.perf_counter()
+        pw.pw_query_batch(g.handle, sp, tp, ep, Lp, dp, params)
+        bq = plain_n / (time.perf_counter() - t0)
+        same = {"queries": plain_n, "batch_queries_per_s": bq, "plain_queries_per_s": plain_qps,
+                "batched_over_plain": bq / plain_qps}
+
+    # ---- the regime where batching matters: the tiny graph (64 queries, eps = 0.2)
+    tiny_regime = None
+    if args.workload != "tiny-er200" and not args.no_tiny:
+        tiny_regime = batched_vs_plain(pw, "tiny-er200", local, params)
 
     # ---- continuous-batching server: burst capacity, then Poisson arrivals ----
     server = None
@@ -610,11 +645,14 @@ def run_ours(args, wl, world, rank, local):
                        "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                        "parallelism": f"query sharding x{world}"},
             "walk_steps_per_s": walk_steps_per_s,
-            "walk_kernel": {1: "per-visit probe evaluation", 2: "per-probe shared-memory table"}.get(walk_mode, "?"),
+            "walk_kernel": {1: "per-visit probe evaluation", 2: "per-probe shared-memory table",
+                            3: "both (chosen per query)"}.get(walk_mode, "?"),
             "autotune": tune,
             "transitions_per_step": transitions_per_step,
             "plain_queries_per_s": plain_qps, "plain_sample": plain_n,
             "batched_over_plain": (value / world) / plain_qps if plain_qps else None,
+            "batched_over_plain_same_queries": same,
+            "batched_over_plain_tiny": tiny_regime,
             "latency_ms": {"plain_p50": pct(50), "plain_p99": pct(99), "batch_step": total_ms / args.steps},
             "server": server,
             "roofline": roofline,
@@ -647,6 +685,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-server", action="store_true")
+    ap.add_argument("--no-tiny", action="store_true", help="skip the tiny-graph batched-vs-plain comparison")
     ap.add_argument("--stabilized", action="store_true", help="L by the stabilization rule (Section 4.3)")
     ap.add_argument("--eps-sweep", action="store_true", help="runtime and error over eps (Fig. 2 protocol)")
     ap.add_argument("--series", action="store_true", help="the GPU truncated series beta^(L) (Lemma 2.3)")

@@ -7,9 +7,10 @@
  * Algorithm 1: for K = B*G Paired-Sign Probes z^(k) (Definition 3.1, generated
  * statelessly as in Section 3.3) it runs R independent pairs of length-L random
  * walks from s and t, forms U_p = sum_i z_{X_i}/d_{X_i} - sum_i z_{~X_i}/d_{~X_i}
- * (Eq. hatphi-def), the U-statistic Q_R = (S1^2 - S2) / (R(R-1)) (Eq. Q-Ustat),
- * and returns the median of the G block means of B probes each
- * (Eq. final-estimator).  The returned value estimates the truncated
+ * (Eq. hatphi-def), the U-statistic Q_R = (S1^2 - S2) / (R(R-1)) (Eq. Q-Ustat)
+ * with S1 = sum_p U_p and S2 = sum_p U_p^2 evaluated exactly and rounded once
+ * to FP64 (so independent of the order in which replicas finish), and returns
+ * the median of the G block means of B probes each (Eq. final-estimator).  The returned value estimates the truncated
  * distance beta^(L) (Lemma 2.3), which is within eps*beta/2 of beta when L is
  * chosen by Eq. uni_l / Theorem 3.8.
  *
@@ -132,9 +133,14 @@ pw_status pw_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, con
 
 /* pw_query_batch: Algorithm 1 for `count` independent queries (host arrays of
  * length count; seeds may be NULL for default seeds), each with the result
- * pw_query gives it.  All walks of all queries run in one persistent launch.  beta_hat and per_query_status (host) receive the
- * results; the return value is PW_OK when the batch ran, even if some queries
- * have a per-query error status.  count == 0 is a no-op. */
+ * pw_query gives it.  The walks of all queries run in two persistent launches
+ * (the probe-table kernel for queries whose probes visit more nodes than a
+ * table costs to build, the per-visit kernel for the rest; the choice is made
+ * per query on the device after the pilot), and the host does not wait for the
+ * device between the input copy and the result copy.  beta_hat and
+ * per_query_status (host) receive the results; the return value is PW_OK when
+ * the batch ran, even if some queries have a per-query error status.
+ * count == 0 is a no-op. */
 pw_status pw_query_batch(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
                          const int32_t* L, const uint64_t* seeds, const pw_params* params, double* beta_hat,
                          int32_t* per_query_status);
@@ -142,7 +148,9 @@ pw_status pw_query_batch(pw_graph* g, int64_t count, const int64_t* s, const int
 /* pw_query_batch_device: as pw_query_batch with every array in device memory
  * and the work ordered on `stream` (a cudaStream_t, NULL for the legacy default
  * stream).  The call returns after the launches are enqueued; it synchronises
- * `stream` once, after the pilot, to size its scratch memory. */
+ * `stream` once, after the budget kernel, to read the batch's total probe count
+ * K, which sizes its scratch memory (8 bytes of Q_R plus 96 of accumulator per
+ * probe; nothing per replica). */
 pw_status pw_query_batch_device(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t,
                                 const double* d_eps, const int32_t* d_L, const uint64_t* d_seeds,
                                 const pw_params* params, double* d_beta_hat, int32_t* d_status, void* stream);
@@ -153,17 +161,19 @@ pw_status pw_query_batch_device(pw_graph* g, int64_t count, const int64_t* d_s, 
  * synchronise the device, are forbidden).  The paper has no counterpart: this
  * is a deployment variant of the same computation, with the same results.
  * The call makes no cudaMalloc, cudaFree or allocating library call: all of
- * its scratch (query plans, offsets, counters, the U_p and Q_R buffers) lives
- * in one static 64 MiB device array that the library holds on every GPU that
- * loads it, until the process exits.  A batch whose scratch exceeds 64 MiB is
- * rejected with PW_ERR_NOMEM (for the n = 100,000 BA graph at eps = 0.1,
- * about four queries per call; for small graphs or large eps, many more).
+ * its scratch (query plans, offsets, counters, pilot sums, the Q_R values and
+ * probe accumulators: about 104 bytes per probe) lives in one static 64 MiB
+ * device array that the library holds on every GPU that loads it, until the
+ * process exits.  A batch whose scratch exceeds 64 MiB is rejected with
+ * PW_ERR_NOMEM (at eps = 0.1 and delta = 0.01 a query has K = 1,850 probes,
+ * about 193 KB, so about 340 such queries fit per call; K grows as 1/eps^2).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call shares the array and clears the counters that must start at
  * zero; calls that overlap on the GPU (other streams or threads) race on it.
  * Arguments, layout and ordering on `stream` are those of
- * pw_query_batch_device; like it, the call synchronises `stream` once. */
+ * pw_query_batch_device; like it, the call synchronises `stream` once, after
+ * the budget kernel. */
 pw_status pw_query_batch_noalloc(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t,
                                  const double* d_eps, const int32_t* d_L, const uint64_t* d_seeds,
                                  const pw_params* params, double* d_beta_hat, int32_t* d_status, void* stream);
@@ -223,9 +233,8 @@ pw_status pw_block_median(const double* block_means, int64_t G, double* out);
  * device work queue.  Queries are admitted while their accumulator memory
  * (8 bytes per probe plus 16 per pilot probe) fits in accum_bytes (at least
  * 1 MiB); later ones wait in a host queue, and a query that needs more than
- * accum_bytes alone fails with PW_ERR_NOMEM.  Requires R <= 4096 and G <= 2048
- * (PILOT clamps R to 4096; other budgets beyond that fail the query with
- * PW_ERR_ARG).
+ * accum_bytes alone fails with PW_ERR_NOMEM.  Requires G <= 2048 (delta above
+ * about 1e-111; a larger FIXED G fails the query with PW_ERR_ARG).
  * pw_server_create: allocates the server on g's device and starts its
  *   scheduler thread; *out receives the handle.
  * pw_server_submit: queues one query (arguments as pw_query; seed NULL for
@@ -279,6 +288,12 @@ pw_status pw_debug_walk(pw_graph* g, int64_t start, int32_t L, uint64_t seed, ui
 pw_status pw_debug_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
                          const pw_params* params, double* beta_hat, uint64_t* budget, double* pilot, double* q,
                          int64_t q_cap, float* u, int64_t u_cap, uint32_t* visits);
+/* pw_debug_exact_sum: S1 = sum u[i] and S2 = sum u[i]^2 (host array of n FP32
+ * values; results to host) through the device accumulator that the walk
+ * kernels use for each probe: exact integer digits, rounded once to the
+ * nearest double, ties to even.  Values must be multiples of 2^-54 below 2^33
+ * in magnitude, as every replica value U_p is (1 <= d < 2^31, L < 2^31). */
+pw_status pw_debug_exact_sum(pw_graph* g, const float* u, int64_t n, double* S1, double* S2);
 /* pw_debug_batch_probe_q: run pw_query_batch and also copy out Q_R of
  * selected probes (host arrays of length n_sel: query index, probe index ->
  * q_sel), and the (K, R) of every query (host uint64 [count][2]). */
@@ -302,7 +317,7 @@ typedef struct pw_profile_stats {
   uint64_t transitions;
   uint64_t pilot_transitions;
   uint64_t queries;
-  int32_t walk_mode;           /* walk kernel of the last batch: 1 per-visit probe evaluation, 2 probe table */
+  int32_t walk_mode;           /* walk kernels of the last batch: 1 per-visit probe evaluation, 2 probe table, 3 both */
   int32_t reserved;
   double series_ms;            /* pw_series_batch passes (32 queries each), summed */
   uint64_t series_steps;       /* sparse steps of those passes: L + 1 per pass */

@@ -1,6 +1,6 @@
 // Budget (Algorithm 1 line 1; Eqs. B-value, G-value, R-value, K-value) and
-// the per-probe U-statistic (Eq. Q-Ustat), shared by the batch pipeline and the
-// server.  FP64 expressions are written operation by operation (no fused
+// the per-probe U-statistic (Eq. Q-Ustat) from the probe's S1 and S2, shared by
+// the batch pipeline and the server.  FP64 expressions are written operation by operation (no fused
 // multiply-add; the library is compiled with --fmad=false as well) in the
 // order the oracle evaluates them, so plans and statistics are bit-identical.
 #pragma once
@@ -92,18 +92,6 @@ __host__ __device__ inline void plan_query(int64_t s, int64_t t, double eps, int
   }
   *out = P;
   if (pilot_out) *pilot_out = PP;
-}
-
-// S1 += u, S2 += u^2 in FP64 (u is an FP32 replica value, so u^2 is exact).
-__host__ __device__ __forceinline__ void accumulate_s(double& S1, double& S2, float u) {
-  const double x = (double)u;
-#ifdef __CUDA_ARCH__
-  S1 = __dadd_rn(S1, x);
-  S2 = __dadd_rn(S2, __dmul_rn(x, x));
-#else
-  S1 = S1 + x;
-  S2 = S2 + x * x;
-#endif
 }
 
 // Q_R = (S1^2 - S2) / (R (R - 1)) (Eq. Q-Ustat).

@@ -23,6 +23,7 @@ pw_status cuda_error(cudaError_t err, const char* what) {
 }
 
 void count_launch() { ++g_launches; }
+void count_launches(int64_t delta) { g_launches += (uint64_t)delta; }
 
 pw_status ensure_buffer(DeviceBuffer& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -69,8 +70,9 @@ void free_workspace(Workspace& ws) {
   free_buffer(ws.plans);
   free_buffer(ws.pilot_plans);
   free_buffer(ws.tile_prefix);
-  free_buffer(ws.pilot_u);
-  free_buffer(ws.u);
+  free_buffer(ws.pilot_s);
+  free_buffer(ws.acc);
+  free_buffer(ws.u_debug);
   free_buffer(ws.q);
   free_buffer(ws.totals);
   free_buffer(ws.counters);

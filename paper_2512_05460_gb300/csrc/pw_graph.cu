@@ -191,6 +191,9 @@ static void destroy(pw_graph* g) {
     cudaEventDestroy(sp.b);
   }
   for (cudaEvent_t e : g->prof.pool) cudaEventDestroy(e);
+  if (g->gcache.exec) cudaGraphExecDestroy(g->gcache.exec);
+  for (pw::Totals* h : g->prof.pending) cudaFreeHost(h);
+  for (pw::Totals* h : g->prof.spare) cudaFreeHost(h);
   if (g->d_rec) cudaFree(g->d_rec);
   if (g->d_node) cudaFree(g->d_node);
   if (g->stream) cudaStreamDestroy(g->stream);

@@ -15,25 +15,31 @@ namespace pw {
 // Per-query plan, one per query of a batch, resident in device memory.
 struct QPlan {
   uint64_t seed;
-  uint64_t tile_begin;   // first walk tile of this query (tiles are 32 replicas of one probe)
-  uint64_t u_begin;      // first U_p slot (probe-major, K*R slots)
+  uint64_t tile_begin;   // first per-visit walk tile of this query (a tile is 32 replicas of one probe)
+  uint64_t acc_begin;    // first per-visit probe accumulator
   uint64_t probe_begin;  // first Q slot (K slots)
+  uint64_t table_begin;  // first entry of this query in the table kernel's probe list
   int32_t s, t;
   int32_t L;
   int32_t status;        // pw_status of this query
   uint32_t K, R, B, G;
   uint32_t chunks;       // ceil(R / 32)
   uint32_t k_begin;      // first probe index (a range of blocks of a sharded query; else 0)
+  uint32_t mode;         // walk kernel of the query's probes: 1 per-visit evaluation, 2 probe table
+  uint32_t pad;
   double eps;
   double sigma2, qbar, theta;  // pilot diagnostics
 };
 
 // Totals written by the scan kernel.
 struct Totals {
-  unsigned long long tiles;
-  unsigned long long u_slots;
-  unsigned long long probes;
-  unsigned long long steps;  // sum of K * R * L (walk pairs times length)
+  unsigned long long tiles;         // per-visit tiles
+  unsigned long long visit_probes;  // probes run by the per-visit kernel
+  unsigned long long table_probes;  // probes run by the table kernel
+  unsigned long long probes;        // all probes (Q slots)
+  unsigned long long steps;         // sum of K * R * L (walk pairs times length)
+  unsigned long long visits;        // sum of 2 K R (L + 1)
+  unsigned long long pad[2];
 };
 
 struct ProfileState {
@@ -44,6 +50,7 @@ struct ProfileState {
   };
   std::vector<Span> spans;
   std::vector<cudaEvent_t> pool;
+  std::vector<Totals*> pending, spare;  // pinned copies of profiled batches' totals
   double walk_ms = 0, pilot_ms = 0, finish_ms = 0, series_ms = 0;
   uint64_t walk_launches = 0, transitions = 0, pilot_transitions = 0, queries = 0, series_steps = 0;
 };
@@ -65,9 +72,19 @@ struct DeviceBuffer {
   size_t bytes = 0;
 };
 
+// A host-array call captured as a CUDA graph: input copy, every launch of the
+// pipeline, result copy.  Replayed while the call's shape (`key`: query count,
+// probe total, budget, cost model, buffer addresses) repeats; a shape seen on
+// two consecutive calls is captured.
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<unsigned char> key, seen;
+  uint64_t launches = 0;  // kernel launches in one replay
+};
+
 struct Workspace {
-  DeviceBuffer plans, pilot_plans, tile_prefix, pilot_u, u, q, totals, counters, queries, results;
-  Totals* host_totals = nullptr;  // pinned
+  DeviceBuffer plans, pilot_plans, tile_prefix, pilot_s, acc, q, totals, counters, queries, results, u_debug;
+  Totals* host_totals = nullptr;  // pinned: totals of the latest batch (valid once last_use has completed)
   void* host_staging = nullptr;   // pinned
   size_t host_staging_bytes = 0;
   cudaEvent_t last_use = nullptr;
@@ -81,9 +98,8 @@ struct pw_graph {
   int32_t d_min = 0, d_max = 0, bipartite = 0;
   std::vector<int32_t> deg;  // host copy of the degrees (host-side query planning)
   int sm_count = 0;
-  int last_walk_mode = 0;  // walk kernel chosen by the last batch (1 on-the-fly, 2 table)
-  // Walk-mode cost model: the probe-table kernel is chosen when
-  //   probes * table_probe_cost < visits * table_visit_gain.
+  // Walk-mode cost model: a query's probes run in the probe-table kernel when
+  //   K * table_probe_cost < 2 K R (L + 1) * table_visit_gain.
   // Defaults (set at load): n and 2.5, in units of one Feistel pass per node
   // (table) against about 2.5 passes per visit (per-visit evaluation);
   // pw_autotune replaces them by nanoseconds measured on this graph.
@@ -92,7 +108,9 @@ struct pw_graph {
   int4* d_rec = nullptr;   // nnz neighbour records
   int4* d_node = nullptr;  // n node records
   cudaStream_t stream = nullptr;
+  int table_grid[2] = {0, 0};  // grid of the table kernel (plain, debug), fixed by n
   std::mutex lock;
+  pw::GraphCache gcache;
   pw::Workspace ws;
   pw::ProfileState prof;
 };
@@ -105,6 +123,7 @@ void prof_begin(pw_graph* g, cudaStream_t stream, cudaEvent_t* a);
 void prof_end(pw_graph* g, cudaStream_t stream, cudaEvent_t a, int kind);
 pw_status cuda_error(cudaError_t err, const char* what);
 void count_launch();
+void count_launches(int64_t delta);  // adjusts the launch count (graph replays, captures)
 pw_status ensure_buffer(DeviceBuffer& b, size_t bytes);
 void free_buffer(DeviceBuffer& b);
 pw_status ensure_host_staging(Workspace& ws, size_t bytes);
@@ -118,17 +137,20 @@ pw_status resolve_budget(const pw_params* params, const pw_graph* g, BudgetArgs*
 // corresponding debug outputs are produced (device pointers sized by caller).
 struct DebugOut {
   uint32_t* visits = nullptr;  // device, n counters of visits by the main walks
+  float* u = nullptr;          // device, K R replica values of query 0 (single-query batches only)
   bool budget_only = false;    // stop after the budget (and pilot) stage
   int64_t g_begin = -1;        // >= 0: run only median-of-means blocks [g_begin, g_end) of query 0
   int64_t g_end = -1;
   double* block_means = nullptr;  // device, g_end - g_begin block means (instead of the median)
-  bool time_walk = false;         // record the main walk kernel's duration and the batch totals below
+  bool time_walk = false;         // record the main walk kernels' duration (walk_ms, after the batch)
   float walk_ms = 0.f;
-  unsigned long long n_probes = 0, n_visits = 0;  // K and 2 sum K R (L+1) of the batch
 };
+// Run a batch whose query arrays are on the device.  total_K: the sum of K over
+// the queries when the caller knows it (host-array calls), else -1, and the
+// batch reads it back from the device once (one synchronisation of `stream`).
 pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t, const double* d_eps,
                     const int32_t* d_L, const uint64_t* d_seeds, const pw_params* params, double* d_beta,
-                    int32_t* d_status, cudaStream_t stream, DebugOut* dbg);
+                    int32_t* d_status, cudaStream_t stream, DebugOut* dbg, int64_t total_K);
 
 }  // namespace pw
 

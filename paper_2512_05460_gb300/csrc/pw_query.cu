@@ -1,7 +1,9 @@
 // Query pipeline of Algorithm 1 on the device:
-//   budget (line 1) -> [pilot walks + pilot budget] -> tile/U/probe offsets ->
-//   persistent walk kernel (lines 2-11) -> per-probe U-statistic (lines 12-14)
-//   -> median of block means (lines 16-20).
+//   budget (line 1) -> [pilot walks + pilot budget] -> per-query walk kernel and
+//   offsets -> walk kernels (lines 2-11), each finishing its probes' Q_R
+//   (lines 12-14) from exact replica sums -> median of block means (lines 16-20).
+// No replica value is stored: a probe's S1 and S2 are exact integer sums
+// (pw_exact.cuh), reduced in registers, warp shuffles and atomics in any order.
 #include <math.h>
 #include <string.h>
 
@@ -10,12 +12,21 @@
 
 #include "pw_budget.cuh"
 #include "pw_device.cuh"
+#include "pw_exact.cuh"
 #include "pw_internal.h"
 #include "pw_walk.cuh"
 
 namespace pw {
 
 constexpr int kWalkThreads = 256;
+
+// Exact S1/S2 digits of a probe run by the per-visit kernel, whose tiles may
+// land on any warp of the grid; `done` counts the probe's finished tiles.
+struct ProbeAcc {
+  unsigned long long d[kSumDigits];
+  unsigned int done;
+  unsigned int pad;
+};
 
 // ---------------------------------------------------------------------------
 // Budget of every query (Algorithm 1 line 1).  PILOT queries get their pilot
@@ -40,10 +51,24 @@ __global__ void budget_init_kernel(int64_t nq, const int64_t* __restrict__ qs, c
   if (pilot) pilot[q] = PP;
 }
 
-// PILOT: R >= 4 sigma^2 / theta (Lemma 3.7) from the pilot replicas, in the
-// oracle's summation order (per probe over replicas, then over probes).
+// Sum of K over the batch (device-array calls size their buffers from it).
+__global__ void sum_k_kernel(const QPlan* __restrict__ plans, int64_t nq, unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long sh[1024];
+  unsigned long long acc = 0;
+  for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) acc += plans[q].K;
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// PILOT: R >= 4 sigma^2 / theta (Lemma 3.7) from the pilot probes' (S1, S2),
+// summed over probes in the oracle's order.
 __global__ void pilot_budget_kernel(int64_t nq, QPlan* __restrict__ plans, const QPlan* __restrict__ pilot,
-                                    const float* __restrict__ pilot_u, BudgetArgs A, const int4* __restrict__ node) {
+                                    const double* __restrict__ pilot_s, BudgetArgs A, const int4* __restrict__ node) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
   const QPlan PP = pilot[q];
@@ -51,70 +76,103 @@ __global__ void pilot_budget_kernel(int64_t nq, QPlan* __restrict__ plans, const
   QPlan& P = plans[q];
   double sum_var = 0.0, sum_q = 0.0;
   for (uint32_t k = 0; k < PP.K; ++k) {
-    const float* u = pilot_u + PP.u_begin + (uint64_t)k * PP.R;
-    double S1 = 0.0, S2 = 0.0;
-    for (uint32_t p = 0; p < PP.R; ++p) accumulate_s(S1, S2, u[p]);
-    pilot_accumulate(sum_var, sum_q, S1, S2, PP.R);
+    const double* sk = pilot_s + 2 * (PP.probe_begin + k);
+    pilot_accumulate(sum_var, sum_q, sk[0], sk[1], PP.R);
   }
   pilot_finish(P, sum_var, sum_q, PP.K, node[P.s].z, node[P.t].z, A);
 }
 
-// Exclusive offsets of tiles (K*chunks), U slots (K*R) and probes (K); one
-// block.  prefix[0..nq] are tile offsets, prefix[nq+1..2nq+1] probe offsets.
+// Walk kernel of each query and the offsets of its work.  A query's probes run
+// in the probe-table kernel when building z^(k) once is cheaper than
+// evaluating it at each of the probe's 2 R (L + 1) visits, by the graph's cost
+// model (forced by walk_mode 1 or 2; the table needs n/8 bytes of shared
+// memory).  prefix holds three arrays of nq + 1 offsets: per-visit tiles
+// (K chunks of 32 replicas), table-kernel probes, and all probes (Q slots).
+struct ModeArgs {
+  int32_t forced;     // 0 auto, 1 per-visit, 2 table
+  int32_t table_ok;   // the table fits in shared memory
+  double probe_cost;  // cost of building one probe's table
+  double visit_gain;  // saving per visit when entries come from the table
+};
+
 __global__ void scan_kernel(QPlan* __restrict__ plans, int64_t nq, unsigned long long* __restrict__ prefix,
-                            Totals* __restrict__ totals) {
-  __shared__ unsigned long long sh[3][1024];
+                            Totals* __restrict__ totals, ModeArgs M) {
+  __shared__ unsigned long long sh[4][1024];
+  __shared__ unsigned long long sh_steps[1024], sh_visits[1024];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int64_t per = (nq + nt - 1) / nt;
   const int64_t b0 = per * tid, b = b0 < nq ? b0 : nq, e = b + per < nq ? b + per : nq;
-  unsigned long long st = 0, su = 0, sp = 0, ss = 0;
-  for (int64_t q = b; q < e; ++q) {
-    const QPlan& P = plans[q];
-    st += (unsigned long long)P.K * P.chunks;
-    su += (unsigned long long)P.K * P.R;
-    sp += P.K;
-    ss += (unsigned long long)P.K * P.R * (unsigned long long)(P.L > 0 ? P.L : 0);
-  }
-  sh[0][tid] = st;
-  sh[1][tid] = su;
-  sh[2][tid] = sp;
-  __shared__ unsigned long long steps_sh[1024];
-  steps_sh[tid] = ss;
-  __syncthreads();
-  if (tid == 0) {
-    unsigned long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    for (int i = 0; i < nt; ++i) {
-      const unsigned long long x0 = sh[0][i], x1 = sh[1][i], x2 = sh[2][i];
-      sh[0][i] = a0;
-      sh[1][i] = a1;
-      sh[2][i] = a2;
-      a0 += x0;
-      a1 += x1;
-      a2 += x2;
-      a3 += steps_sh[i];
-    }
-    totals->tiles = a0;
-    totals->u_slots = a1;
-    totals->probes = a2;
-    totals->steps = a3;
-    prefix[nq] = a0;
-    prefix[2 * nq + 1] = a2;
-  }
-  __syncthreads();
-  st = sh[0][tid];
-  su = sh[1][tid];
-  sp = sh[2][tid];
+  unsigned long long a[4] = {0, 0, 0, 0}, steps = 0, visits = 0;
   for (int64_t q = b; q < e; ++q) {
     QPlan& P = plans[q];
-    P.tile_begin = st;
-    P.u_begin = su;
-    P.probe_begin = sp;
-    prefix[q] = st;
-    prefix[nq + 1 + q] = sp;
-    st += (unsigned long long)P.K * P.chunks;
-    su += (unsigned long long)P.K * P.R;
-    sp += P.K;
+    const double v = 2.0 * (double)P.R * (double)(P.L + 1);
+    uint32_t mode = M.forced != 0 ? (uint32_t)M.forced
+                                  : (M.probe_cost < v * M.visit_gain ? 2u : 1u);
+    if (!M.table_ok) mode = 1u;
+    P.mode = mode;
+    const unsigned long long K = P.K;
+    a[0] += mode == 1u ? K * P.chunks : 0ull;  // per-visit tiles
+    a[1] += mode == 1u ? K : 0ull;             // per-visit probes (accumulators)
+    a[2] += mode == 2u ? K : 0ull;             // table probes
+    a[3] += K;                                 // all probes
+    steps += K * P.R * (unsigned long long)(P.L > 0 ? P.L : 0);
+    visits += 2ull * K * P.R * (unsigned long long)(P.L + 1);
   }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sh[j][tid] = a[j];
+  sh_steps[tid] = steps;
+  sh_visits[tid] = visits;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long run[4] = {0, 0, 0, 0}, st = 0, vi = 0;
+    for (int i = 0; i < nt; ++i) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const unsigned long long x = sh[j][i];
+        sh[j][i] = run[j];
+        run[j] += x;
+      }
+      st += sh_steps[i];
+      vi += sh_visits[i];
+    }
+    totals->tiles = run[0];
+    totals->visit_probes = run[1];
+    totals->table_probes = run[2];
+    totals->probes = run[3];
+    totals->steps = st;
+    totals->visits = vi;
+    prefix[nq] = run[0];
+    prefix[(nq + 1) + nq] = run[2];
+    prefix[2 * (nq + 1) + nq] = run[3];
+  }
+  __syncthreads();
+  unsigned long long o[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) o[j] = sh[j][tid];
+  for (int64_t q = b; q < e; ++q) {
+    QPlan& P = plans[q];
+    const unsigned long long K = P.K;
+    P.tile_begin = o[0];
+    P.acc_begin = o[1];
+    P.table_begin = o[2];
+    P.probe_begin = o[3];
+    prefix[q] = o[0];
+    prefix[(nq + 1) + q] = o[2];
+    prefix[2 * (nq + 1) + q] = o[3];
+    o[0] += P.mode == 1u ? K * P.chunks : 0ull;
+    o[1] += P.mode == 1u ? K : 0ull;
+    o[2] += P.mode == 2u ? K : 0ull;
+    o[3] += K;
+  }
+}
+
+// Accumulators of the per-visit probes start at zero.
+__global__ void zero_acc_kernel(ProbeAcc* __restrict__ acc, const Totals* __restrict__ totals) {
+  const unsigned long long words = totals->visit_probes * (sizeof(ProbeAcc) / 8);
+  unsigned long long* w = (unsigned long long*)acc;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    w[i] = 0ull;
 }
 
 __device__ __forceinline__ int64_t find_segment(const unsigned long long* __restrict__ prefix, int64_t nq,
@@ -134,25 +192,32 @@ struct WalkArgs {
   const int4* rec;
   const int4* node;
   const QPlan* plans;
-  const unsigned long long* tile_prefix;
+  const unsigned long long* tile_prefix;   // per-visit tiles
+  const unsigned long long* table_prefix;  // table-kernel probes
   const Totals* totals;
-  unsigned long long* tile_counter;
-  float* u;
-  uint32_t* visits;
+  unsigned long long* counter;  // claim cursor of this launch
+  ProbeAcc* acc;                // per-visit probe accumulators (main stage)
+  double* q;                    // Q_R per probe (main stage) or (S1, S2) per probe (pilot)
+  float* u_debug;               // optional: replica values of query 0
+  uint32_t* visits;             // optional: visit counts
   int64_t nq;
   uint32_t n;
   uint32_t walk_tag, probe_tag;
 };
 
-// Persistent walk kernel: each warp pops tiles (query, probe k, 32 replicas)
-// from a device counter until the work runs out; lane l runs replica 32c + l.
-template <bool DEBUG>
+// Persistent per-visit walk kernel: each warp pops tiles (query, probe k, 32
+// replicas) from a device counter until the work runs out; lane l runs
+// replica 32c + l with probe entries evaluated at each visit.  The warp sums
+// its tile's replicas exactly; a pilot tile is a whole probe (R0 <= 32) and
+// writes (S1, S2); a main tile adds its digits to the probe's accumulator and
+// the probe's last tile computes Q_R.
+template <bool DEBUG, bool PILOT>
 __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkArgs A) {
   const uint32_t lane = threadIdx.x & 31u;
   const unsigned long long total = A.totals->tiles;
   for (;;) {
     unsigned long long tile = 0;
-    if (lane == 0) tile = atomicAdd(A.tile_counter, 1ull);
+    if (lane == 0) tile = atomicAdd(A.counter, 1ull);
     tile = __shfl_sync(0xffffffffu, tile, 0);
     if (tile >= total) return;
     const int64_t q = find_segment(A.tile_prefix, A.nq, tile);
@@ -162,43 +227,69 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkArgs A) {
     const uint32_t kl = (uint32_t)(local / chunks);
     const uint32_t c = (uint32_t)(local - (unsigned long long)kl * chunks);
     const uint32_t p = c * 32u + lane;
-    if (p >= R) continue;
     const uint32_t k = P.k_begin + kl;
-    const Probe pr = make_probe(A.n, P.seed, k, A.probe_tag);
-    const uint64_t pair = (uint64_t)k * R + p;
-    const ZOnTheFly zp{pr};
-    const float U = walk_pair<DEBUG>(A.rec, A.node, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
-    A.u[P.u_begin + (uint64_t)kl * R + p] = U;
+    SumDigits sum;
+    sum_clear(sum);
+    if (p < R) {
+      const Probe pr = make_probe(A.n, P.seed, k, A.probe_tag);
+      const uint64_t pair = (uint64_t)k * R + p;
+      const ZOnTheFly zp{pr};
+      const float U = walk_pair<DEBUG>(A.rec, A.node, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
+      if (DEBUG && A.u_debug && q == 0) A.u_debug[(uint64_t)kl * R + p] = U;
+      sum_add(sum, U);
+    }
+    sum_warp_reduce(sum);
+    if (lane != 0) continue;
+    if (PILOT) {
+      double S1, S2;
+      sum_round(sum.d, S1, S2);
+      A.q[2 * (P.probe_begin + kl)] = S1;
+      A.q[2 * (P.probe_begin + kl) + 1] = S2;
+    } else {
+      ProbeAcc* pa = A.acc + P.acc_begin + kl;
+      sum_atomic_add(pa->d, sum);
+      __threadfence();
+      if (atomicAdd(&pa->done, 1u) + 1u == chunks) {
+        __threadfence();
+        long long d[kSumDigits];
+#pragma unroll
+        for (int j = 0; j < kSumDigits; ++j) d[j] = (long long)__ldcg(pa->d + j);
+        double S1, S2;
+        sum_round(d, S1, S2);
+        A.q[P.probe_begin + kl] = u_statistic(S1, S2, R);
+      }
+    }
   }
 }
 
-// Probe-major kernel: a block claims one probe k of one query, writes the
+// Probe-table walk kernel: a block claims one probe k of one query, writes the
 // whole vector z^(k) into a shared-memory table (sign bits plus the zero set;
-// one Feistel cycle-walk per node), then its warps run the
-// probe's 32-replica tiles reading z from the table.  Same values as the
-// on-the-fly kernel; cheaper whenever a probe's walks visit more nodes than
-// the graph has (2 R (L+1) > n).
+// one Feistel cycle-walk per node), then its warps run the probe's 32-replica
+// tiles reading z from the table, add each tile's exact sums into the block's
+// digits, and the block writes the probe's Q_R.  Same values as the per-visit
+// kernel; cheaper whenever a probe's walks visit more nodes than the Feistel
+// domain has (2 R (L+1) > 2^b).
 template <bool DEBUG>
-__global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A,
-                                                                  const unsigned long long* __restrict__ probe_prefix,
-                                                                  unsigned long long* __restrict__ probe_counter) {
+__global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A) {
   extern __shared__ uint32_t tab[];
   __shared__ unsigned long long sh_probe;
+  __shared__ unsigned long long sh_sum[kSumDigits];
   __shared__ uint32_t sh_tile;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t n = A.n;
-  const unsigned long long total = A.totals->probes;
+  const unsigned long long total = A.totals->table_probes;
   for (;;) {
     if (threadIdx.x == 0) {
-      sh_probe = atomicAdd(probe_counter, 1ull);
+      sh_probe = atomicAdd(A.counter, 1ull);
       sh_tile = 0;
     }
+    if (threadIdx.x < kSumDigits) sh_sum[threadIdx.x] = 0ull;
     __syncthreads();
     const unsigned long long j = sh_probe;
     if (j >= total) return;
-    const int64_t q = find_segment(probe_prefix, A.nq, j);
+    const int64_t q = find_segment(A.table_prefix, A.nq, j);
     const QPlan& P = A.plans[q];
-    const uint32_t kl = (uint32_t)(j - P.probe_begin);
+    const uint32_t kl = (uint32_t)(j - P.table_begin);
     const uint32_t k = P.k_begin + kl;
     build_probe_table(make_probe(n, P.seed, k, A.probe_tag), tab, n);
     __syncthreads();
@@ -210,31 +301,55 @@ __global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A,
       c = __shfl_sync(0xffffffffu, c, 0);
       if (c >= chunks) break;
       const uint32_t p = c * 32u + lane;
+      SumDigits sum;
+      sum_clear(sum);
       if (p < R) {
         const uint64_t pair = (uint64_t)k * R + p;
         const float U = walk_pair_table<DEBUG>(A.rec, A.node, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
-        A.u[P.u_begin + (uint64_t)kl * R + p] = U;
+        if (DEBUG && A.u_debug && q == 0) A.u_debug[(uint64_t)kl * R + p] = U;
+        sum_add(sum, U);
       }
+      sum_warp_reduce(sum);
+      if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < kSumDigits; ++d)
+          if (sum.d[d] != 0) atomicAdd(sh_sum + d, (unsigned long long)sum.d[d]);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long d[kSumDigits];
+#pragma unroll
+      for (int i = 0; i < kSumDigits; ++i) d[i] = (long long)sh_sum[i];
+      double S1, S2;
+      sum_round(d, S1, S2);
+      A.q[P.probe_begin + kl] = u_statistic(S1, S2, R);
     }
     __syncthreads();
   }
 }
 
-// Q_R per probe (Eq. Q-Ustat): S1, S2 in FP64 over replicas in order.
-__global__ void probe_finish_kernel(const QPlan* __restrict__ plans, int64_t nq,
-                                    const unsigned long long* __restrict__ probe_prefix,
-                                    const Totals* __restrict__ totals, const float* __restrict__ u,
-                                    double* __restrict__ qbuf) {
-  const unsigned long long total = totals->probes;
-  for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < total;
-       j += (unsigned long long)gridDim.x * blockDim.x) {
-    const int64_t q = find_segment(probe_prefix, nq, j);
-    const QPlan& P = plans[q];
-    const unsigned long long k = j - P.probe_begin;
-    const float* x = u + P.u_begin + k * P.R;
-    double S1 = 0.0, S2 = 0.0;
-    for (uint32_t p = 0; p < P.R; ++p) accumulate_s(S1, S2, x[p]);
-    qbuf[j] = u_statistic(S1, S2, P.R);
+// Exact S1, S2 of caller values through the walk kernels' accumulator (tests):
+// lanes add strided values, warps reduce, shared 64-bit atomics combine.
+__global__ void debug_exact_sum_kernel(const float* __restrict__ u, int64_t n, double* __restrict__ out) {
+  __shared__ unsigned long long acc[kSumDigits];
+  if (threadIdx.x < kSumDigits) acc[threadIdx.x] = 0ull;
+  __syncthreads();
+  const int64_t rounds = (n + blockDim.x - 1) / blockDim.x;
+  for (int64_t r = 0; r < rounds; ++r) {
+    const int64_t i = r * blockDim.x + threadIdx.x;
+    SumDigits sum;
+    sum_clear(sum);
+    if (i < n) sum_add(sum, u[i]);
+    sum_warp_reduce(sum);
+    if ((threadIdx.x & 31u) == 0u)
+      for (int d = 0; d < kSumDigits; ++d) atomicAdd(acc + d, (unsigned long long)sum.d[d]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long d[kSumDigits];
+    for (int j = 0; j < kSumDigits; ++j) d[j] = (long long)acc[j];
+    sum_round(d, out[0], out[1]);
   }
 }
 
@@ -299,18 +414,15 @@ __global__ void block_means_kernel(const QPlan* __restrict__ plans, const double
   if (threadIdx.x == 0) status[0] = P.status;
 }
 
-static int walk_grid(pw_graph* g, bool debug) {
-  static int occ[2] = {0, 0};
-  int& o = occ[debug ? 1 : 0];
-  if (o == 0) {
+template <bool DEBUG, bool PILOT>
+static int walk_grid(pw_graph* g) {
+  static int occ = 0;
+  if (occ == 0) {
     int nb = 0;
-    if (debug)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<true>, kWalkThreads, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<false>, kWalkThreads, 0);
-    o = nb > 0 ? nb : 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<DEBUG, PILOT>, kWalkThreads, 0);
+    occ = nb > 0 ? nb : 1;
   }
-  return g->sm_count * o;
+  return g->sm_count * occ;
 }
 
 static cudaEvent_t prof_event(pw_graph* g) {
@@ -343,150 +455,148 @@ void prof_end(pw_graph* g, cudaStream_t stream, cudaEvent_t a, int kind) {
 static size_t table_bytes(const pw_graph* g) { return sizeof(uint32_t) * (size_t)table_words((uint32_t)g->n); }
 static constexpr size_t kMaxTableBytes = 200 * 1024;
 
-static int table_grid(pw_graph* g, bool debug, size_t smem) {
-  int nb = 0;
-  if (debug) {
-    cudaFuncSetAttribute(walk_table_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_table_kernel<true>, kWalkThreads, smem);
-  } else {
-    cudaFuncSetAttribute(walk_table_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_table_kernel<false>, kWalkThreads, smem);
+template <bool DEBUG>
+static int table_grid(pw_graph* g, size_t smem) {
+  int& grid = g->table_grid[DEBUG ? 1 : 0];
+  if (grid == 0) {
+    int nb = 0;
+    cudaFuncSetAttribute(walk_table_kernel<DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_table_kernel<DEBUG>, kWalkThreads, smem);
+    grid = g->sm_count * (nb > 0 ? nb : 1);
   }
-  return g->sm_count * (nb > 0 ? nb : 1);
+  return grid;
 }
 
-// Walk kernel of a batch: the caller's walk_mode, else the graph's cost model
-// (probe table when probes * table_probe_cost < visits * table_visit_gain,
-// 2 R (L+1) visits per probe); the table needs its bits in shared memory.
-static int pick_walk_mode(const pw_graph* g, const pw_params* params, const Totals& T) {
-  int mode = params ? params->walk_mode : 0;
-  if (mode == 0) {
-    const double visits = 2.0 * ((double)T.steps + (double)T.u_slots);
-    mode = (table_bytes(g) <= kMaxTableBytes && (double)T.probes * g->table_probe_cost < visits * g->table_visit_gain)
-               ? 2
-               : 1;
-  }
-  if (mode == 2 && table_bytes(g) > kMaxTableBytes) mode = 1;
-  return mode;
+template <bool DEBUG, bool PILOT>
+static pw_status launch_walk(pw_graph* g, cudaStream_t stream, const WalkArgs& a) {
+  walk_kernel<DEBUG, PILOT><<<walk_grid<DEBUG, PILOT>(g), kWalkThreads, 0, stream>>>(a);
+  count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  return PW_OK;
 }
 
-static pw_status launch_walk_table(pw_graph* g, cudaStream_t stream, bool debug, const WalkArgs& a,
-                                   const unsigned long long* probe_prefix, unsigned long long* probe_counter) {
+template <bool DEBUG>
+static pw_status launch_table(pw_graph* g, cudaStream_t stream, const WalkArgs& a) {
   const size_t smem = table_bytes(g);
-  const int grid = table_grid(g, debug, smem);
-  if (debug)
-    walk_table_kernel<true><<<grid, kWalkThreads, smem, stream>>>(a, probe_prefix, probe_counter);
-  else
-    walk_table_kernel<false><<<grid, kWalkThreads, smem, stream>>>(a, probe_prefix, probe_counter);
+  walk_table_kernel<DEBUG><<<table_grid<DEBUG>(g, smem), kWalkThreads, smem, stream>>>(a);
   count_launch();
   PW_CUDA_TRY(cudaGetLastError());
   return PW_OK;
 }
 
-static pw_status launch_walk(pw_graph* g, cudaStream_t stream, bool debug, const WalkArgs& a) {
-  const int grid = walk_grid(g, debug);
-  if (debug)
-    walk_kernel<true><<<grid, kWalkThreads, 0, stream>>>(a);
-  else
-    walk_kernel<false><<<grid, kWalkThreads, 0, stream>>>(a);
-  count_launch();
-  PW_CUDA_TRY(cudaGetLastError());
-  return PW_OK;
+// Device scratch of one batch.  Sizes depend on the query count, the pilot
+// shape and the sum of K; nothing depends on R, so a batch never waits for its
+// pilot to size memory.
+struct BatchBuffers {
+  QPlan* plans;
+  QPlan* pplans;
+  unsigned long long* prefix;    // 6 (nq + 1): main tiles, table probes, probes; then the pilot's three
+  Totals* totals;                // [0] main, [1] pilot
+  unsigned long long* counters;  // [0] main per-visit tiles, [1] pilot tiles, [2] table probes
+  double* pilot_s;               // (S1, S2) per pilot probe
+  double* q;                     // Q_R per probe
+  ProbeAcc* acc;                 // per-visit probe accumulators
+};
+
+struct BatchSizes {
+  size_t plans, prefix, totals, counters, pilot_s, q, acc;
+};
+
+static BatchSizes batch_sizes(size_t nq, size_t total_K, const BudgetArgs& ba) {
+  BatchSizes z;
+  z.plans = sizeof(QPlan) * nq;
+  z.prefix = sizeof(unsigned long long) * 6 * (nq + 1);
+  z.totals = sizeof(Totals) * 2;
+  z.counters = 64;
+  z.pilot_s = ba.mode == PW_BUDGET_PILOT ? sizeof(double) * 2 * nq * (size_t)ba.K0 : 16;
+  z.q = sizeof(double) * (total_K ? total_K : 1);
+  z.acc = sizeof(ProbeAcc) * (total_K ? total_K : 1);
+  return z;
 }
 
-pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t, const double* d_eps,
-                    const int32_t* d_L, const uint64_t* d_seeds, const pw_params* params, double* d_beta,
-                    int32_t* d_status, cudaStream_t stream, DebugOut* dbg) {
-  BudgetArgs ba;
-  pw_status st = resolve_budget(params, g, &ba, nullptr);
-  if (st != PW_OK) return st;
-  if (count < 0) return set_error(PW_ERR_ARG, "count < 0");
-  if (count == 0) return PW_OK;
-  Workspace& ws = g->ws;
-  PW_CUDA_TRY(cudaStreamWaitEvent(stream, ws.last_use, 0));
-  const bool pilot = ba.mode == PW_BUDGET_PILOT;
-  const size_t nq = (size_t)count;
-  if ((st = ensure_buffer(ws.plans, sizeof(QPlan) * nq)) != PW_OK) return st;
-  if ((st = ensure_buffer(ws.pilot_plans, sizeof(QPlan) * nq)) != PW_OK) return st;
-  if ((st = ensure_buffer(ws.tile_prefix, sizeof(unsigned long long) * 4 * (nq + 1))) != PW_OK) return st;
-  if ((st = ensure_buffer(ws.totals, sizeof(Totals) * 2)) != PW_OK) return st;
-  if ((st = ensure_buffer(ws.counters, 64)) != PW_OK) return st;
-  QPlan* plans = (QPlan*)ws.plans.ptr;
-  QPlan* pplans = (QPlan*)ws.pilot_plans.ptr;
-  unsigned long long* prefix = (unsigned long long*)ws.tile_prefix.ptr;
-  unsigned long long* pprefix = prefix + 2 * (nq + 1);
-  Totals* totals = (Totals*)ws.totals.ptr;
-  unsigned long long* counters = (unsigned long long*)ws.counters.ptr;
-  PW_CUDA_TRY(cudaMemsetAsync(counters, 0, 64, stream));
+// First stage: counters cleared, plans of every query (and their pilots).
+static pw_status enqueue_budget(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t, const double* d_eps,
+                                const int32_t* d_L, const uint64_t* d_seeds, const BudgetArgs& ba,
+                                const BatchBuffers& B, cudaStream_t stream) {
+  PW_CUDA_TRY(cudaMemsetAsync(B.counters, 0, 64, stream));
   const int qthreads = 128;
   const int qblocks = (int)((count + qthreads - 1) / qthreads);
   budget_init_kernel<<<qblocks, qthreads, 0, stream>>>(count, d_s, d_t, d_eps, d_L, d_seeds, ba, g->n, g->d_node,
-                                                       plans, pilot ? pplans : nullptr);
+                                                       B.plans, ba.mode == PW_BUDGET_PILOT ? B.pplans : nullptr);
   count_launch();
   PW_CUDA_TRY(cudaGetLastError());
+  return PW_OK;
+}
+
+// The rest of the pipeline: pilot, walk kernels, median.  No host
+// synchronisation: every size it needs was fixed by batch_sizes.
+static pw_status enqueue_walks(pw_graph* g, int64_t count, const pw_params* params, const BudgetArgs& ba,
+                               const BatchBuffers& B, double* d_beta, int32_t* d_status, cudaStream_t stream,
+                               DebugOut* dbg) {
+  const size_t nq = (size_t)count;
+  const bool pilot = ba.mode == PW_BUDGET_PILOT;
+  const int qthreads = 128;
+  const int qblocks = (int)((count + qthreads - 1) / qthreads);
+  unsigned long long* prefix = B.prefix;
+  unsigned long long* pprefix = B.prefix + 3 * (nq + 1);
   WalkArgs wa;
+  memset(&wa, 0, sizeof wa);
   wa.rec = g->d_rec;
   wa.node = g->d_node;
   wa.nq = count;
   wa.n = (uint32_t)g->n;
-  wa.visits = nullptr;
+  pw_status st;
   if (pilot) {
-    const size_t pslots = nq * (size_t)ba.K0 * (size_t)ba.R0;
-    if ((st = ensure_buffer(ws.pilot_u, sizeof(float) * pslots)) != PW_OK) return st;
-    scan_kernel<<<1, 1024, 0, stream>>>(pplans, count, pprefix, totals + 1);
+    ModeArgs pm{1, 0, 0.0, 0.0};
+    scan_kernel<<<1, 1024, 0, stream>>>(B.pplans, count, pprefix, B.totals + 1, pm);
     count_launch();
-    wa.plans = pplans;
+    wa.plans = B.pplans;
     wa.tile_prefix = pprefix;
-    wa.totals = totals + 1;
-    wa.tile_counter = counters + 1;
-    wa.u = (float*)ws.pilot_u.ptr;
+    wa.totals = B.totals + 1;
+    wa.counter = B.counters + 1;
+    wa.q = B.pilot_s;
     wa.walk_tag = kTagWalkPilot;
     wa.probe_tag = kTagProbePilot;
     cudaEvent_t ev;
     prof_begin(g, stream, &ev);
-    if ((st = launch_walk(g, stream, false, wa)) != PW_OK) return st;
+    if ((st = launch_walk<false, true>(g, stream, wa)) != PW_OK) return st;
     prof_end(g, stream, ev, 1);
     if (g->prof.enabled) g->prof.pilot_transitions += 2ull * nq * (uint64_t)ba.K0 * (uint64_t)ba.R0;
-    pilot_budget_kernel<<<qblocks, qthreads, 0, stream>>>(count, plans, pplans, (const float*)ws.pilot_u.ptr, ba,
-                                                          g->d_node);
+    pilot_budget_kernel<<<qblocks, qthreads, 0, stream>>>(count, B.plans, B.pplans, B.pilot_s, ba, g->d_node);
     count_launch();
     PW_CUDA_TRY(cudaGetLastError());
   }
   const bool sharded = dbg && dbg->g_begin >= 0;
   if (sharded) {
-    restrict_blocks_kernel<<<1, 1, 0, stream>>>(plans, (uint32_t)dbg->g_begin, (uint32_t)dbg->g_end);
+    restrict_blocks_kernel<<<1, 1, 0, stream>>>(B.plans, (uint32_t)dbg->g_begin, (uint32_t)dbg->g_end);
     count_launch();
     PW_CUDA_TRY(cudaGetLastError());
   }
-  scan_kernel<<<1, 1024, 0, stream>>>(plans, count, prefix, totals);
+  const bool table_ok = table_bytes(g) <= kMaxTableBytes;
+  ModeArgs M{params ? params->walk_mode : 0, table_ok ? 1 : 0, g->table_probe_cost, g->table_visit_gain};
+  if (M.forced < 0 || M.forced > 2) return set_error(PW_ERR_ARG, "walk_mode must be 0, 1 or 2");
+  scan_kernel<<<1, 1024, 0, stream>>>(B.plans, count, prefix, B.totals, M);
   count_launch();
   PW_CUDA_TRY(cudaGetLastError());
-  PW_CUDA_TRY(cudaMemcpyAsync(ws.host_totals, totals, sizeof(Totals), cudaMemcpyDeviceToHost, stream));
-  PW_CUDA_TRY(cudaStreamSynchronize(stream));
-  const Totals T = *ws.host_totals;
-  if (dbg && dbg->budget_only) {
-    PW_CUDA_TRY(cudaEventRecord(ws.last_use, stream));
-    return PW_OK;
-  }
-  if ((st = ensure_buffer(ws.u, sizeof(float) * (size_t)T.u_slots)) != PW_OK) return st;
-  if ((st = ensure_buffer(ws.q, sizeof(double) * (size_t)T.probes)) != PW_OK) return st;
-  const bool debug = dbg && dbg->visits;
-  wa.plans = plans;
+  if (dbg && dbg->budget_only) return PW_OK;
+  zero_acc_kernel<<<g->sm_count * 4, 256, 0, stream>>>(B.acc, B.totals);
+  count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  const bool debug = dbg && (dbg->visits || dbg->u);
+  wa.plans = B.plans;
   wa.tile_prefix = prefix;
-  wa.totals = totals;
-  wa.tile_counter = counters;
-  wa.u = (float*)ws.u.ptr;
-  wa.visits = debug ? dbg->visits : nullptr;
+  wa.table_prefix = prefix + (nq + 1);
+  wa.totals = B.totals;
+  wa.acc = B.acc;
+  wa.q = B.q;
+  wa.visits = dbg ? dbg->visits : nullptr;
+  wa.u_debug = dbg ? dbg->u : nullptr;
   wa.walk_tag = kTagWalk;
   wa.probe_tag = kTagProbe;
-  const int mode = pick_walk_mode(g, params, T);
-  g->last_walk_mode = mode;
   cudaEvent_t ev_walk;
   prof_begin(g, stream, &ev_walk);
   cudaEvent_t tw[2] = {nullptr, nullptr};
   if (dbg && dbg->time_walk) {
-    dbg->n_probes = T.probes;
-    dbg->n_visits = 2ull * (T.steps + T.u_slots);
     PW_CUDA_TRY(cudaEventCreate(&tw[0]));
     cudaError_t e = cudaEventCreate(&tw[1]);
     if (e == cudaSuccess) e = cudaEventRecord(tw[0], stream);
@@ -496,11 +606,14 @@ pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_
       return cuda_error(e, "walk timing events");
     }
   }
-  if (T.tiles > 0) {
-    if (mode == 2)
-      st = launch_walk_table(g, stream, debug, wa, prefix + nq + 1, counters + 2);
-    else
-      st = launch_walk(g, stream, debug, wa);
+  st = PW_OK;
+  if (table_ok) {
+    wa.counter = B.counters + 2;
+    st = debug ? launch_table<true>(g, stream, wa) : launch_table<false>(g, stream, wa);
+  }
+  if (st == PW_OK) {
+    wa.counter = B.counters;
+    st = debug ? launch_walk<true, false>(g, stream, wa) : launch_walk<false, false>(g, stream, wa);
   }
   if (tw[0]) {
     cudaError_t e = st == PW_OK ? cudaEventRecord(tw[1], stream) : cudaSuccess;
@@ -513,33 +626,221 @@ pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_
   if (st != PW_OK) return st;
   prof_end(g, stream, ev_walk, 0);
   if (g->prof.enabled) {
-    g->prof.walk_launches += T.tiles > 0 ? 1 : 0;
-    g->prof.transitions += 2ull * T.steps;
+    g->prof.walk_launches += 1;
     g->prof.queries += nq;
   }
   cudaEvent_t ev_fin;
   prof_begin(g, stream, &ev_fin);
-  if (T.probes > 0) {
-    const int fthreads = 128;
-    const unsigned long long want = (T.probes + fthreads - 1) / fthreads;
-    const int fblocks = (int)std::min<unsigned long long>(want, (unsigned long long)g->sm_count * 64);
-    probe_finish_kernel<<<fblocks, fthreads, 0, stream>>>(plans, count, prefix + nq + 1, totals,
-                                                          (const float*)ws.u.ptr, (double*)ws.q.ptr);
-    count_launch();
-    PW_CUDA_TRY(cudaGetLastError());
-  }
   if (sharded)
-    block_means_kernel<<<1, 128, 0, stream>>>(plans, (const double*)ws.q.ptr, dbg->block_means, d_status);
+    block_means_kernel<<<1, 128, 0, stream>>>(B.plans, B.q, dbg->block_means, d_status);
   else
-    mom_kernel<<<(unsigned)count, 128, 0, stream>>>(plans, (const double*)ws.q.ptr, d_beta, d_status);
+    mom_kernel<<<(unsigned)count, 128, 0, stream>>>(B.plans, B.q, d_beta, d_status);
   count_launch();
   PW_CUDA_TRY(cudaGetLastError());
   prof_end(g, stream, ev_fin, 2);
+  return PW_OK;
+}
+
+// Totals of a finished batch for the profile (pinned copy, read by pw_profile).
+static pw_status prof_totals(pw_graph* g, const Totals* d_totals, cudaStream_t stream) {
+  ProfileState& P = g->prof;
+  if (!P.enabled) return PW_OK;
+  Totals* h = nullptr;
+  if (!P.spare.empty()) {
+    h = P.spare.back();
+    P.spare.pop_back();
+  } else {
+    PW_CUDA_TRY(cudaMallocHost(&h, sizeof(Totals)));
+  }
+  P.pending.push_back(h);
+  PW_CUDA_TRY(cudaMemcpyAsync(h, d_totals, sizeof(Totals), cudaMemcpyDeviceToHost, stream));
+  return PW_OK;
+}
+
+static pw_status batch_buffers(pw_graph* g, size_t nq, size_t total_K, const BudgetArgs& ba, BatchBuffers* B) {
+  Workspace& ws = g->ws;
+  const BatchSizes z = batch_sizes(nq, total_K, ba);
+  pw_status st;
+  if ((st = ensure_buffer(ws.plans, z.plans)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.pilot_plans, z.plans)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.tile_prefix, z.prefix)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.totals, z.totals)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.counters, z.counters)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.pilot_s, z.pilot_s)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.q, z.q)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.acc, z.acc)) != PW_OK) return st;
+  B->plans = (QPlan*)ws.plans.ptr;
+  B->pplans = (QPlan*)ws.pilot_plans.ptr;
+  B->prefix = (unsigned long long*)ws.tile_prefix.ptr;
+  B->totals = (Totals*)ws.totals.ptr;
+  B->counters = (unsigned long long*)ws.counters.ptr;
+  B->pilot_s = (double*)ws.pilot_s.ptr;
+  B->q = (double*)ws.q.ptr;
+  B->acc = (ProbeAcc*)ws.acc.ptr;
+  return PW_OK;
+}
+
+// Sum of K over the batch, read back from the device (one synchronisation).
+static pw_status device_total_K(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t,
+                                const double* d_eps, const int32_t* d_L, const uint64_t* d_seeds, const BudgetArgs& ba,
+                                cudaStream_t stream, size_t* total_K) {
+  Workspace& ws = g->ws;
+  pw_status st;
+  if ((st = ensure_buffer(ws.plans, sizeof(QPlan) * (size_t)count)) != PW_OK) return st;
+  if ((st = ensure_buffer(ws.counters, 64)) != PW_OK) return st;
+  const int qthreads = 128;
+  const int qblocks = (int)((count + qthreads - 1) / qthreads);
+  budget_init_kernel<<<qblocks, qthreads, 0, stream>>>(count, d_s, d_t, d_eps, d_L, d_seeds, ba, g->n, g->d_node,
+                                                       (QPlan*)ws.plans.ptr, nullptr);
+  count_launch();
+  unsigned long long* out = (unsigned long long*)ws.counters.ptr + 7;
+  sum_k_kernel<<<1, 1024, 0, stream>>>((const QPlan*)ws.plans.ptr, count, out);
+  count_launch();
+  PW_CUDA_TRY(cudaGetLastError());
+  PW_CUDA_TRY(cudaMemcpyAsync(&ws.host_totals->pad[0], out, 8, cudaMemcpyDeviceToHost, stream));
+  PW_CUDA_TRY(cudaStreamSynchronize(stream));
+  *total_K = (size_t)ws.host_totals->pad[0];
+  return PW_OK;
+}
+
+// Every stage of a batch whose scratch is sized, then a copy of its totals.
+static pw_status enqueue_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t,
+                               const double* d_eps, const int32_t* d_L, const uint64_t* d_seeds,
+                               const pw_params* params, const BudgetArgs& ba, const BatchBuffers& B, double* d_beta,
+                               int32_t* d_status, cudaStream_t stream, DebugOut* dbg) {
+  pw_status st;
+  if ((st = enqueue_budget(g, count, d_s, d_t, d_eps, d_L, d_seeds, ba, B, stream)) != PW_OK) return st;
+  if ((st = enqueue_walks(g, count, params, ba, B, d_beta, d_status, stream, dbg)) != PW_OK) return st;
+  PW_CUDA_TRY(cudaMemcpyAsync(g->ws.host_totals, B.totals, sizeof(Totals), cudaMemcpyDeviceToHost, stream));
+  return prof_totals(g, B.totals, stream);
+}
+
+pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t, const double* d_eps,
+                    const int32_t* d_L, const uint64_t* d_seeds, const pw_params* params, double* d_beta,
+                    int32_t* d_status, cudaStream_t stream, DebugOut* dbg, int64_t total_K) {
+  BudgetArgs ba;
+  pw_status st = resolve_budget(params, g, &ba, nullptr);
+  if (st != PW_OK) return st;
+  if (count < 0) return set_error(PW_ERR_ARG, "count < 0");
+  if (count == 0) return PW_OK;
+  Workspace& ws = g->ws;
+  PW_CUDA_TRY(cudaStreamWaitEvent(stream, ws.last_use, 0));
+  size_t K = 0;
+  if (total_K >= 0) {
+    K = (size_t)total_K;
+  } else if ((st = device_total_K(g, count, d_s, d_t, d_eps, d_L, d_seeds, ba, stream, &K)) != PW_OK) {
+    return st;
+  }
+  BatchBuffers B;
+  if ((st = batch_buffers(g, (size_t)count, K, ba, &B)) != PW_OK) return st;
+  if (dbg && dbg->u && count != 1) return set_error(PW_ERR_ARG, "replica output needs a single-query batch");
+  if ((st = enqueue_batch(g, count, d_s, d_t, d_eps, d_L, d_seeds, params, ba, B, d_beta, d_status, stream, dbg)) !=
+      PW_OK)
+    return st;
   PW_CUDA_TRY(cudaEventRecord(ws.last_use, stream));
   return PW_OK;
 }
 
+// Sum of K over host-array queries, from the same plan as the device
+// (invalid queries and s == t contribute 0).
+static size_t host_total_K(const pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
+                           const int32_t* L, const BudgetArgs& ba) {
+  size_t K = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    const bool in = s[i] >= 0 && s[i] < g->n && t[i] >= 0 && t[i] < g->n;
+    QPlan P;
+    plan_query(s[i], t[i], eps[i], L[i], 0, g->n, in ? g->deg[(size_t)s[i]] : 1, in ? g->deg[(size_t)t[i]] : 1, ba,
+               &P, nullptr);
+    K += P.K;
+  }
+  return K;
+}
+
+template <class T>
+static void key_put(std::vector<unsigned char>& k, const T& v) {
+  const unsigned char* p = (const unsigned char*)&v;
+  k.insert(k.end(), p, p + sizeof(T));
+}
+
+// A host-array call through a CUDA graph: the staged inputs at h (in_bytes)
+// go in, the results come back to ho (out_bytes).  Returns PW_PENDING
+// without running anything when this shape has not been seen on the previous
+// call (the caller then runs it eagerly); captures it on its second
+// consecutive call; replays it afterwards.
+static pw_status graph_batch(pw_graph* g, int64_t count, const char* h, char* ho, size_t in_bytes, size_t out_bytes,
+                             const pw_params* params, const BudgetArgs& ba, size_t total_K) {
+  Workspace& ws = g->ws;
+  GraphCache& gc = g->gcache;
+  BatchBuffers B;
+  pw_status st = batch_buffers(g, (size_t)count, total_K, ba, &B);  // allocations stay outside the capture
+  if (st != PW_OK) return st;
+  const bool table_ok = table_bytes(g) <= kMaxTableBytes;
+  if (table_ok) table_grid<false>(g, table_bytes(g));
+  walk_grid<false, false>(g);
+  walk_grid<false, true>(g);
+  std::vector<unsigned char> key;
+  key_put(key, count);
+  key_put(key, total_K);
+  key_put(key, ba);
+  key_put(key, params ? params->walk_mode : 0);
+  key_put(key, g->table_probe_cost);
+  key_put(key, g->table_visit_gain);
+  key_put(key, B);
+  key_put(key, ws.queries.ptr);
+  key_put(key, ws.results.ptr);
+  key_put(key, (const void*)h);
+  if (!(gc.exec && key == gc.key)) {
+    if (key != gc.seen) {
+      gc.seen = key;
+      return PW_PENDING;
+    }
+    const uint64_t before = pw_launch_count(0);
+    PW_CUDA_TRY(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    char* d = (char*)ws.queries.ptr;
+    const size_t nq = (size_t)count;
+    cudaError_t e = cudaMemcpyAsync(d, h, in_bytes, cudaMemcpyHostToDevice, g->stream);
+    st = e == cudaSuccess ? PW_OK : cuda_error(e, "graph input copy");
+    if (st == PW_OK)
+      st = enqueue_batch(g, count, (const int64_t*)d, (const int64_t*)(d + nq * 8), (const double*)(d + nq * 16),
+                         (const int32_t*)(d + nq * 32), (const uint64_t*)(d + nq * 24), params, ba, B,
+                         (double*)ws.results.ptr, (int32_t*)((char*)ws.results.ptr + nq * 8), g->stream, nullptr);
+    if (st == PW_OK) {
+      e = cudaMemcpyAsync(ho, ws.results.ptr, out_bytes, cudaMemcpyDeviceToHost, g->stream);
+      if (e != cudaSuccess) st = cuda_error(e, "graph result copy");
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(g->stream, &graph);
+    const uint64_t captured = pw_launch_count(0) - before;
+    count_launches(-(int64_t)captured);  // nothing ran during the capture
+    if (st == PW_OK && ec != cudaSuccess) st = cuda_error(ec, "cudaStreamEndCapture");
+    if (st == PW_OK) {
+      if (gc.exec) cudaGraphExecDestroy(gc.exec);
+      gc.exec = nullptr;
+      e = cudaGraphInstantiate(&gc.exec, graph, 0);
+      if (e != cudaSuccess) {
+        gc.exec = nullptr;
+        st = cuda_error(e, "cudaGraphInstantiate");
+      }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st != PW_OK) {
+      gc.key.clear();
+      gc.seen.clear();
+      return st;
+    }
+    gc.key = key;
+    gc.launches = captured;
+  }
+  PW_CUDA_TRY(cudaGraphLaunch(gc.exec, g->stream));
+  count_launches((int64_t)gc.launches);
+  PW_CUDA_TRY(cudaEventRecord(ws.last_use, g->stream));
+  PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return PW_OK;
+}
+
 // Host-array batch: stage inputs in pinned memory, run, copy results back.
+// Nothing between the input copy and the result copy waits for the host, so a
+// call whose shape repeats runs as one CUDA graph.
 static pw_status host_batch(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
                             const int32_t* L, const uint64_t* seeds, const pw_params* params, double* beta,
                             int32_t* status, DebugOut* dbg) {
@@ -549,7 +850,9 @@ static pw_status host_batch(pw_graph* g, int64_t count, const int64_t* s, const 
   Workspace& ws = g->ws;
   const size_t nq = (size_t)count;
   const size_t in_bytes = nq * (8 + 8 + 8 + 8 + 4), out_bytes = nq * (8 + 4);
-  pw_status st;
+  BudgetArgs ba;
+  pw_status st = resolve_budget(params, g, &ba, nullptr);
+  if (st != PW_OK) return st;
   if ((st = ensure_host_staging(ws, in_bytes + out_bytes + 64)) != PW_OK) return st;
   if ((st = ensure_buffer(ws.queries, in_bytes + 64)) != PW_OK) return st;
   if ((st = ensure_buffer(ws.results, out_bytes + 64)) != PW_OK) return st;
@@ -562,22 +865,32 @@ static pw_status host_batch(pw_graph* g, int64_t count, const int64_t* s, const 
   if (seeds) {
     memcpy(h + nq * 24, seeds, nq * 8);
   } else {
-    BudgetArgs ba;
-    if ((st = resolve_budget(params, g, &ba, nullptr)) != PW_OK) return st;
     for (size_t i = 0; i < nq; ++i)
       ((uint64_t*)(h + nq * 24))[i] = default_seed(ba.global_seed, s[i], t[i], eps[i], L[i]);
   }
   memcpy(h + nq * 32, L, nq * 4);
+  const size_t K = host_total_K(g, count, s, t, eps, L, ba);
   char* d = (char*)ws.queries.ptr;
-  PW_CUDA_TRY(cudaMemcpyAsync(d, h, in_bytes, cudaMemcpyHostToDevice, g->stream));
   double* d_beta = (double*)ws.results.ptr;
   int32_t* d_status = (int32_t*)((char*)ws.results.ptr + nq * 8);
+  char* ho = h + in_bytes;
+  if (!dbg && !g->prof.enabled) {
+    st = graph_batch(g, count, h, ho, in_bytes, out_bytes, params, ba, K);
+    if (st == PW_OK) {
+      memcpy(beta, ho, nq * 8);
+      memcpy(status, ho + nq * 8, nq * 4);
+    }
+    if (st != PW_PENDING) return st;  // PENDING: shape not seen twice yet, run it eagerly
+  }
+  PW_CUDA_TRY(cudaMemcpyAsync(d, h, in_bytes, cudaMemcpyHostToDevice, g->stream));
   st = run_batch(g, count, (const int64_t*)d, (const int64_t*)(d + nq * 8), (const double*)(d + nq * 16),
                  (const int32_t*)(d + nq * 32), (const uint64_t*)(d + nq * 24), params, d_beta, d_status, g->stream,
-                 dbg);
+                 dbg, (int64_t)K);
   if (st != PW_OK) return st;
-  if (dbg && dbg->budget_only) return PW_OK;
-  char* ho = h + in_bytes;
+  if (dbg && dbg->budget_only) {
+    PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return PW_OK;
+  }
   PW_CUDA_TRY(cudaMemcpyAsync(ho, ws.results.ptr, out_bytes, cudaMemcpyDeviceToHost, g->stream));
   PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
   memcpy(beta, ho, nq * 8);
@@ -589,6 +902,13 @@ static pw_status copy_plan(pw_graph* g, int64_t q, QPlan* out) {
   PW_CUDA_TRY(cudaMemcpyAsync(out, (QPlan*)g->ws.plans.ptr + q, sizeof(QPlan), cudaMemcpyDeviceToHost, g->stream));
   PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
   return PW_OK;
+}
+
+// Walk kernels that ran in the latest batch: 1 per-visit, 2 table, 3 both.
+static int last_walk_mode(const pw_graph* g) {
+  const Totals* T = g->ws.host_totals;
+  if (!T) return 0;
+  return (T->tiles > 0 ? 1 : 0) | (T->table_probes > 0 ? 2 : 0);
 }
 
 }  // namespace pw
@@ -615,7 +935,7 @@ pw_status pw_query_batch_device(pw_graph* g, int64_t count, const int64_t* d_s, 
   std::lock_guard<std::mutex> guard(g->lock);
   PW_CUDA_TRY(cudaSetDevice(g->device));
   return run_batch(g, count, d_s, d_t, d_eps, d_L, d_seeds, params, d_beta_hat, d_status, (cudaStream_t)stream,
-                   nullptr);
+                   nullptr, -1);
 }
 
 pw_status pw_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
@@ -679,6 +999,17 @@ pw_status pw_debug_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t 
   pw_status st = resolve_budget(params, g, &ba, nullptr);
   if (st != PW_OK) return st;
   const uint64_t sd = seed ? *seed : default_seed(ba.global_seed, s, t, eps, L);
+  // pass 1: the budget alone, to size the replica output
+  DebugOut pre;
+  pre.budget_only = true;
+  int32_t qst = 0;
+  st = host_batch(g, 1, &s, &t, &eps, &L, &sd, params, beta_hat, &qst, &pre);
+  if (st != PW_OK) return st;
+  QPlan P0;
+  if ((st = copy_plan(g, 0, &P0)) != PW_OK) return st;
+  const uint64_t KR0 = (uint64_t)P0.K * P0.R;
+  if ((q && (uint64_t)q_cap < P0.K) || (u && (uint64_t)u_cap < KR0)) return set_error(PW_ERR_ARG, "q_cap or u_cap too small");
+  // pass 2: the whole query, with replica values and visit counts
   DebugOut dbg;
   DeviceBuffer vis;
   if (visits) {
@@ -686,7 +1017,10 @@ pw_status pw_debug_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t 
     PW_CUDA_TRY(cudaMemsetAsync(vis.ptr, 0, sizeof(uint32_t) * (size_t)g->n, g->stream));
     dbg.visits = (uint32_t*)vis.ptr;
   }
-  int32_t qst = 0;
+  if (u && KR0) {
+    if ((st = ensure_buffer(g->ws.u_debug, sizeof(float) * (size_t)KR0)) != PW_OK) return st;
+    dbg.u = (float*)g->ws.u_debug.ptr;
+  }
   st = host_batch(g, 1, &s, &t, &eps, &L, &sd, params, beta_hat, &qst, &dbg);
   if (st == PW_OK && qst != PW_OK) st = set_error((pw_status)qst, "query rejected");
   QPlan P;
@@ -705,18 +1039,12 @@ pw_status pw_debug_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t 
       pilot[2] = P.theta;
     }
     const uint64_t K = P.K, KR = (uint64_t)P.K * P.R;
-    if ((q && (uint64_t)q_cap < K) || (u && (uint64_t)u_cap < KR)) {
-      st = set_error(PW_ERR_ARG, "q_cap or u_cap too small");
-    } else {
-      if (q && K) cudaMemcpyAsync(q, (double*)g->ws.q.ptr + P.probe_begin, sizeof(double) * K, cudaMemcpyDeviceToHost,
-                                  g->stream);
-      if (u && KR) cudaMemcpyAsync(u, (float*)g->ws.u.ptr + P.u_begin, sizeof(float) * KR, cudaMemcpyDeviceToHost,
-                                   g->stream);
-      if (visits)
-        cudaMemcpyAsync(visits, vis.ptr, sizeof(uint32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, g->stream);
-      cudaError_t e = cudaStreamSynchronize(g->stream);
-      if (e != cudaSuccess) st = cuda_error(e, "debug copy-out");
-    }
+    if (q && K) cudaMemcpyAsync(q, (double*)g->ws.q.ptr + P.probe_begin, sizeof(double) * K, cudaMemcpyDeviceToHost,
+                                g->stream);
+    if (u && KR) cudaMemcpyAsync(u, g->ws.u_debug.ptr, sizeof(float) * KR, cudaMemcpyDeviceToHost, g->stream);
+    if (visits) cudaMemcpyAsync(visits, vis.ptr, sizeof(uint32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, g->stream);
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) st = cuda_error(e, "debug copy-out");
   }
   free_buffer(vis);
   return st;
@@ -828,6 +1156,12 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
   std::lock_guard<std::mutex> guard(g->lock);
   PW_CUDA_TRY(cudaSetDevice(g->device));
   ProfileState& P = g->prof;
+  if (!P.pending.empty()) PW_CUDA_TRY(cudaEventSynchronize(g->ws.last_use));
+  for (Totals* h : P.pending) {
+    P.transitions += 2ull * h->steps;
+    P.spare.push_back(h);
+  }
+  P.pending.clear();
   for (auto& sp : P.spans) {
     PW_CUDA_TRY(cudaEventSynchronize(sp.b));
     float ms = 0.f;
@@ -845,7 +1179,8 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
     out->transitions = P.transitions;
     out->pilot_transitions = P.pilot_transitions;
     out->queries = P.queries;
-    out->walk_mode = g->last_walk_mode;
+    PW_CUDA_TRY(cudaEventSynchronize(g->ws.last_use));
+    out->walk_mode = last_walk_mode(g);
     out->reserved = 0;
     out->series_ms = P.series_ms;
     out->series_steps = P.series_steps;
@@ -882,23 +1217,30 @@ pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_
   std::vector<int32_t> L4(nq);
   for (size_t i = 0; i < nq; ++i) L4[i] = L[i] >= 4 ? L[i] / 4 : 4 * L[i];
   // one warm-up and one timed run of the sample in walk kernel `mode`
-  auto timed = [&](int mode, const int32_t* Ls, DebugOut* d) -> pw_status {
+  // probes and visits of each timed run, from its totals
+  struct Run {
+    DebugOut d;
+    double n_probes = 0, n_visits = 0;
+  };
+  auto timed = [&](int mode, const int32_t* Ls, Run* r) -> pw_status {
     p.walk_mode = mode;
     for (int rep = 0; rep < 2; ++rep) {
-      *d = DebugOut();
-      d->time_walk = true;
-      const pw_status st = host_batch(g, count, s, t, eps, Ls, seeds, &p, beta.data(), status.data(), d);
+      r->d = DebugOut();
+      r->d.time_walk = true;
+      const pw_status st = host_batch(g, count, s, t, eps, Ls, seeds, &p, beta.data(), status.data(), &r->d);
       if (st != PW_OK) return st;
     }
+    r->n_probes = (double)g->ws.host_totals->probes;
+    r->n_visits = (double)g->ws.host_totals->visits;
     for (size_t i = 0; i < nq; ++i)
       if (status[i] != PW_OK) return set_error((pw_status)status[i], "pw_autotune: a sample query failed");
     return PW_OK;
   };
-  DebugOut dv, dt, dq;
+  Run dv, dt, dq;
   pw_status st = timed(1, L, &dv);
   if (st != PW_OK) return st;
-  out->sample_ms[0] = dv.walk_ms;
-  out->visit_ns = dv.n_visits ? 1e6 * dv.walk_ms / (double)dv.n_visits : 0.0;
+  out->sample_ms[0] = dv.d.walk_ms;
+  out->visit_ns = dv.n_visits > 0 ? 1e6 * dv.d.walk_ms / dv.n_visits : 0.0;
   out->sample_mode = 1;
   if (table_bytes(g) > kMaxTableBytes) {
     g->table_visit_gain = 0.0;  // the table cannot be built: always per-visit
@@ -908,11 +1250,11 @@ pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_
   out->table_available = 1;
   if ((st = timed(2, L, &dt)) != PW_OK) return st;
   if ((st = timed(2, L4.data(), &dq)) != PW_OK) return st;
-  out->sample_ms[1] = dt.walk_ms;
-  out->sample_ms[2] = dq.walk_ms;
+  out->sample_ms[1] = dt.d.walk_ms;
+  out->sample_ms[2] = dq.d.walk_ms;
   // solve  T = P c + V w  for the two table runs (times in ns)
-  const double T2 = 1e6 * dt.walk_ms, T3 = 1e6 * dq.walk_ms;
-  const double P2 = (double)dt.n_probes, P3 = (double)dq.n_probes, V2 = (double)dt.n_visits, V3 = (double)dq.n_visits;
+  const double T2 = 1e6 * dt.d.walk_ms, T3 = 1e6 * dq.d.walk_ms;
+  const double P2 = dt.n_probes, P3 = dq.n_probes, V2 = dt.n_visits, V3 = dq.n_visits;
   const double det = P2 * V3 - P3 * V2;
   double c = 0.0, w = 0.0;
   if (det != 0.0) {
@@ -933,8 +1275,33 @@ pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_
   g->table_probe_cost = c;
   g->table_visit_gain = out->visit_ns - w;
   g->tuned = 1;
-  const double Vs = (double)dv.n_visits, Ps = (double)dv.n_probes;
+  const double Vs = dv.n_visits, Ps = dv.n_probes;
   out->sample_mode = Ps * g->table_probe_cost < Vs * g->table_visit_gain ? 2 : 1;
+  return PW_OK;
+}
+
+pw_status pw_debug_exact_sum(pw_graph* g, const float* u, int64_t n, double* S1, double* S2) {
+  if (!g || (!u && n > 0) || !S1 || !S2 || n < 0) return set_error(PW_ERR_ARG, "NULL argument or n < 0");
+  std::lock_guard<std::mutex> guard(g->lock);
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  DeviceBuffer b;
+  pw_status st = ensure_buffer(b, sizeof(float) * (size_t)n + 64);
+  if (st != PW_OK) return st;
+  float* du = (float*)((char*)b.ptr + 64);
+  double* dout = (double*)b.ptr;
+  cudaError_t e = n ? cudaMemcpyAsync(du, u, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, g->stream) : cudaSuccess;
+  if (e == cudaSuccess) {
+    debug_exact_sum_kernel<<<1, 256, 0, g->stream>>>(du, n, dout);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  double out[2] = {0.0, 0.0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof out, cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  free_buffer(b);
+  if (e != cudaSuccess) return cuda_error(e, "pw_debug_exact_sum");
+  *S1 = out[0];
+  *S2 = out[1];
   return PW_OK;
 }
 
@@ -979,13 +1346,13 @@ namespace pw {
 // real-time service that forbids allocator calls (cudaMalloc can block and
 // synchronise the device) in its request path, or code that runs where the
 // CUDA allocator is off limits.  pw_query_batch_noalloc serves them: its
-// scratch (query plans, offsets, counters, the U_p and Q_R buffers) is carved
-// out of the file-scope array below, so the call itself makes no cudaMalloc,
-// cudaFree or allocating library call.  The array holds kNoAllocScratchBytes
-// on every GPU that loads the library, until the process exits.  Every call
-// shares it: calls that overlap on the GPU (different streams, or another
-// thread) race on its contents; the counters that must start at zero are
-// cleared by each call.
+// scratch (query plans, offsets, counters, pilot sums, Q_R values and probe
+// accumulators) is carved out of the file-scope array below, so the call
+// itself makes no cudaMalloc, cudaFree or allocating library call.  The array
+// holds kNoAllocScratchBytes on every GPU that loads the library, until the
+// process exits.  Every call shares it: calls that overlap on the GPU
+// (different streams, or another thread) race on its contents; the counters
+// and accumulators that must start at zero are cleared by each call.
 // ---------------------------------------------------------------------------
 constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;
 static __device__ __align__(256) unsigned char pw_noalloc_scratch[kNoAllocScratchBytes];
@@ -1030,100 +1397,54 @@ extern "C" pw_status pw_query_batch_noalloc(pw_graph* g, int64_t count, const in
   unsigned char* base = nullptr;
   if ((st = noalloc_scratch(g->device, &base)) != PW_OK) return st;
   cudaStream_t stream = (cudaStream_t)stream_ptr;
-  const bool pilot = ba.mode == PW_BUDGET_PILOT;
   const size_t nq = (size_t)count;
-  // fixed part of the layout: plans, pilot plans, offsets, totals, counters, pilot U
+  // plans and counters first: the sum of K over the batch sizes the rest
   size_t off = 0;
   const size_t o_plans = off;
   off = align256(off + sizeof(QPlan) * nq);
-  const size_t o_pplans = off;
-  off = align256(off + sizeof(QPlan) * nq);
-  const size_t o_prefix = off;
-  off = align256(off + sizeof(unsigned long long) * 4 * (nq + 1));
-  const size_t o_totals = off;
-  off = align256(off + sizeof(Totals) * 2);
   const size_t o_counters = off;
   off = align256(off + 64);
-  const size_t o_pilot_u = off;
-  off = align256(off + (pilot ? sizeof(float) * nq * (size_t)ba.K0 * (size_t)ba.R0 : 0));
   if (off > kNoAllocScratchBytes)
     return set_error(PW_ERR_NOMEM, "pw_query_batch_noalloc: batch needs more than the 64 MiB static scratch");
-  QPlan* plans = (QPlan*)(base + o_plans);
-  QPlan* pplans = (QPlan*)(base + o_pplans);
-  unsigned long long* prefix = (unsigned long long*)(base + o_prefix);
-  unsigned long long* pprefix = prefix + 2 * (nq + 1);
-  Totals* totals = (Totals*)(base + o_totals);
-  unsigned long long* counters = (unsigned long long*)(base + o_counters);
-  float* pilot_u = (float*)(base + o_pilot_u);
+  BatchBuffers B;
+  B.plans = (QPlan*)(base + o_plans);
+  B.counters = (unsigned long long*)(base + o_counters);
   PW_CUDA_TRY(cudaStreamWaitEvent(stream, g->ws.last_use, 0));
-  PW_CUDA_TRY(cudaMemsetAsync(counters, 0, 64, stream));
   const int qthreads = 128;
   const int qblocks = (int)((count + qthreads - 1) / qthreads);
   budget_init_kernel<<<qblocks, qthreads, 0, stream>>>(count, d_s, d_t, d_eps, d_L, d_seeds, ba, g->n, g->d_node,
-                                                       plans, pilot ? pplans : nullptr);
+                                                       B.plans, nullptr);
+  count_launch();
+  sum_k_kernel<<<1, 1024, 0, stream>>>(B.plans, count, B.counters + 7);
   count_launch();
   PW_CUDA_TRY(cudaGetLastError());
-  WalkArgs wa;
-  wa.rec = g->d_rec;
-  wa.node = g->d_node;
-  wa.nq = count;
-  wa.n = (uint32_t)g->n;
-  wa.visits = nullptr;
-  if (pilot) {
-    scan_kernel<<<1, 1024, 0, stream>>>(pplans, count, pprefix, totals + 1);
-    count_launch();
-    wa.plans = pplans;
-    wa.tile_prefix = pprefix;
-    wa.totals = totals + 1;
-    wa.tile_counter = counters + 1;
-    wa.u = pilot_u;
-    wa.walk_tag = kTagWalkPilot;
-    wa.probe_tag = kTagProbePilot;
-    if ((st = launch_walk(g, stream, false, wa)) != PW_OK) return st;
-    pilot_budget_kernel<<<qblocks, qthreads, 0, stream>>>(count, plans, pplans, pilot_u, ba, g->d_node);
-    count_launch();
-    PW_CUDA_TRY(cudaGetLastError());
-  }
-  scan_kernel<<<1, 1024, 0, stream>>>(plans, count, prefix, totals);
-  count_launch();
-  PW_CUDA_TRY(cudaGetLastError());
-  PW_CUDA_TRY(cudaMemcpyAsync(g->ws.host_totals, totals, sizeof(Totals), cudaMemcpyDeviceToHost, stream));
+  PW_CUDA_TRY(cudaMemcpyAsync(&g->ws.host_totals->pad[0], B.counters + 7, 8, cudaMemcpyDeviceToHost, stream));
   PW_CUDA_TRY(cudaStreamSynchronize(stream));
-  const Totals T = *g->ws.host_totals;
-  const size_t o_u = off;
-  off = align256(off + sizeof(float) * (size_t)T.u_slots);
+  const BatchSizes z = batch_sizes(nq, (size_t)g->ws.host_totals->pad[0], ba);
+  const size_t o_pplans = off;
+  off = align256(off + z.plans);
+  const size_t o_prefix = off;
+  off = align256(off + z.prefix);
+  const size_t o_totals = off;
+  off = align256(off + z.totals);
+  const size_t o_pilot = off;
+  off = align256(off + z.pilot_s);
   const size_t o_q = off;
-  off = align256(off + sizeof(double) * (size_t)T.probes);
+  off = align256(off + z.q);
+  const size_t o_acc = off;
+  off = align256(off + z.acc);
   if (off > kNoAllocScratchBytes)
-    return set_error(PW_ERR_NOMEM, "pw_query_batch_noalloc: the walks of this batch need more than the 64 MiB "
-                                   "static scratch (U_p and Q_R buffers); split the batch");
-  float* u = (float*)(base + o_u);
-  double* qbuf = (double*)(base + o_q);
-  const int mode = pick_walk_mode(g, params, T);
-  g->last_walk_mode = mode;
-  wa.plans = plans;
-  wa.tile_prefix = prefix;
-  wa.totals = totals;
-  wa.tile_counter = counters;
-  wa.u = u;
-  wa.walk_tag = kTagWalk;
-  wa.probe_tag = kTagProbe;
-  if (T.tiles > 0) {
-    st = mode == 2 ? launch_walk_table(g, stream, false, wa, prefix + nq + 1, counters + 2)
-                   : launch_walk(g, stream, false, wa);
-    if (st != PW_OK) return st;
-  }
-  if (T.probes > 0) {
-    const int fthreads = 128;
-    const unsigned long long want = (T.probes + fthreads - 1) / fthreads;
-    const int fblocks = (int)std::min<unsigned long long>(want, (unsigned long long)g->sm_count * 64);
-    probe_finish_kernel<<<fblocks, fthreads, 0, stream>>>(plans, count, prefix + nq + 1, totals, u, qbuf);
-    count_launch();
-    PW_CUDA_TRY(cudaGetLastError());
-  }
-  mom_kernel<<<(unsigned)count, 128, 0, stream>>>(plans, qbuf, d_beta_hat, d_status);
-  count_launch();
-  PW_CUDA_TRY(cudaGetLastError());
+    return set_error(PW_ERR_NOMEM, "pw_query_batch_noalloc: the probes of this batch need more than the 64 MiB "
+                                   "static scratch (104 bytes per probe); split the batch");
+  B.pplans = (QPlan*)(base + o_pplans);
+  B.prefix = (unsigned long long*)(base + o_prefix);
+  B.totals = (Totals*)(base + o_totals);
+  B.pilot_s = (double*)(base + o_pilot);
+  B.q = (double*)(base + o_q);
+  B.acc = (ProbeAcc*)(base + o_acc);
+  if ((st = enqueue_budget(g, count, d_s, d_t, d_eps, d_L, d_seeds, ba, B, stream)) != PW_OK) return st;
+  if ((st = enqueue_walks(g, count, params, ba, B, d_beta_hat, d_status, stream, nullptr)) != PW_OK) return st;
+  PW_CUDA_TRY(cudaMemcpyAsync(g->ws.host_totals, B.totals, sizeof(Totals), cudaMemcpyDeviceToHost, stream));
   PW_CUDA_TRY(cudaEventRecord(g->ws.last_use, stream));
   return PW_OK;
 }

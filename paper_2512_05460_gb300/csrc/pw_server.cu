@@ -1,9 +1,10 @@
 // Continuous-batching server: one persistent kernel fed by a device work queue.
 //
-// Work unit = one probe job (query slot, stage, probe k): a block runs all R
-// replicas of probe k (its warps take 32-replica tiles), keeps the R values of
-// U_p in shared memory, and writes Q_R of the probe (Eq. Q-Ustat) or, in the
-// pilot stage, the probe's (S1, S2).  The block that completes the last pilot
+// Work unit = one probe job (query slot, stage, probes k .. k + count - 1): a
+// block runs all R replicas of its probes (its warps take 32-replica tiles),
+// adds each tile's exact replica sums into the block's digits of that probe
+// (pw_exact.cuh), and writes Q_R of each probe (Eq. Q-Ustat) or, in the pilot
+// stage, the probe's (S1, S2).  The block that completes the last pilot
 // probe of a query computes R (Lemma 3.7 condition) and publishes the query's
 // main stage; the block that completes the last main probe takes the median of
 // the block means (Eq. final-estimator) and writes the result to host-mapped
@@ -28,6 +29,7 @@
 
 #include "pw_budget.cuh"
 #include "pw_device.cuh"
+#include "pw_exact.cuh"
 #include "pw_internal.h"
 #include "pw_walk.cuh"
 
@@ -35,8 +37,9 @@ namespace pw {
 
 constexpr uint32_t kStagePilot = 0, kStageMain = 1;
 constexpr int kServerThreads = 256;
-constexpr uint32_t kServerRmax = 4096;  // U_p of one probe lives in shared memory
-constexpr uint32_t kServerGmax = 2048;  // block means reuse the U_p buffer as doubles
+constexpr uint32_t kServerGmax = 2048;  // block means of the final job live in shared memory
+constexpr size_t kServerMeansBytes = sizeof(double) * kServerGmax;
+constexpr uint32_t kJobProbes = 8;      // at most 8 probes per job
 
 struct SlotDev {
   QPlan plan;          // main plan; R written by the pilot transition in PILOT mode
@@ -170,8 +173,8 @@ template <bool TABLE>
 __global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(ServerArgs A) {
   extern __shared__ uint32_t smem[];
   uint32_t* tab = smem;
-  float* su = (float*)(smem + A.table_words);
-  double* means = (double*)su;
+  double* means = (double*)(smem + A.table_words);  // table_words is a multiple of 4
+  __shared__ unsigned long long j_sum[kJobProbes][kSumDigits];
   __shared__ uint32_t j_slot, j_stage, j_k, j_count, j_valid, j_last, j_tile;
   const uint32_t lane = threadIdx.x & 31u;
   if (threadIdx.x == 0) atomicMax(A.last_claim, global_ns());  // a fresh launch starts its idle clock
@@ -186,6 +189,7 @@ __global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(S
       j_tile = 0;
       j_last = 0;
     }
+    if (threadIdx.x < kJobProbes * kSumDigits) (&j_sum[0][0])[threadIdx.x] = 0ull;
     __syncthreads();
     if (!j_valid) return;
     const uint32_t slot = j_slot, stage = j_stage, k0 = j_k, nprobe = j_count;
@@ -199,7 +203,8 @@ __global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(S
     const uint32_t chunks = (R + 31u) / 32u;
     if (TABLE && table) build_probe_table(make_probe(A.n, P.seed, k0, probe_tag), tab, A.n);
     __syncthreads();
-    // tiles of 32 replicas over the job's probes; U_p of probe k0 + j at su[j R + p]
+    // tiles of 32 replicas over the job's probes; each tile's exact sums go
+    // into the digits of its probe j (any order gives the same digits)
     for (;;) {
       uint32_t c = 0;
       if (lane == 0) c = atomicAdd(&j_tile, 1u);
@@ -207,6 +212,8 @@ __global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(S
       if (c >= chunks * nprobe) break;
       const uint32_t j = c / chunks, p = (c - j * chunks) * 32u + lane;
       const uint32_t k = k0 + j;
+      SumDigits sum;
+      sum_clear(sum);
       if (p < R) {
         const uint64_t pair = (uint64_t)k * R + p;
         float U;
@@ -216,14 +223,23 @@ __global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(S
         } else {
           U = server_walk_visit(A.rec, A.node, A.n, walk_tag, probe_tag, P.s, P.t, P.L, P.seed, k, pair);
         }
-        su[j * R + p] = U;
+        sum_add(sum, U);
+      }
+      sum_warp_reduce(sum);
+      if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < kSumDigits; ++d)
+          if (sum.d[d] != 0) atomicAdd(&j_sum[j][d], (unsigned long long)sum.d[d]);
       }
     }
     __syncthreads();
-    if (threadIdx.x < nprobe) {  // one thread per probe: S1, S2 in replica order
+    if (threadIdx.x < nprobe) {  // one thread per probe: S1, S2 rounded from the exact digits
       const uint32_t j = threadIdx.x, k = k0 + j;
-      double S1 = 0.0, S2 = 0.0;
-      for (uint32_t p = 0; p < R; ++p) accumulate_s(S1, S2, su[j * R + p]);
+      long long dj[kSumDigits];
+#pragma unroll
+      for (int d = 0; d < kSumDigits; ++d) dj[d] = (long long)j_sum[j][d];
+      double S1, S2;
+      sum_round(dj, S1, S2);
       if (pilot) {
         __stcg(S->ps + 2 * k, S1);
         __stcg(S->ps + 2 * k + 1, S2);
@@ -398,7 +414,7 @@ static ServerArgs server_args(pw_server* sv) {
   a.rec = sv->g->d_rec;
   a.node = sv->g->d_node;
   a.n = (uint32_t)sv->g->n;
-  a.table_words = (uint32_t)((sv->smem - sizeof(float) * kServerRmax) / sizeof(uint32_t));
+  a.table_words = (uint32_t)((sv->smem - kServerMeansBytes) / sizeof(uint32_t));
   a.slots = sv->d_slots;
   a.heads = sv->d_ctl;
   a.dtail = sv->d_ctl + 2;
@@ -426,7 +442,7 @@ static bool admit(pw_server* sv, const Request& rq) {
   QPlan P, PP;
   plan_query(rq.s, rq.t, rq.eps, rq.L, rq.seed, g->n, ok_ids ? g->deg[(size_t)rq.s] : 1,
              ok_ids ? g->deg[(size_t)rq.t] : 1, sv->ba, &P, &PP);
-  if (P.status == PW_OK && (P.R > kServerRmax || P.G > kServerGmax)) P.status = PW_ERR_ARG;
+  if (P.status == PW_OK && P.G > kServerGmax) P.status = PW_ERR_ARG;
   if (P.status != PW_OK || P.K == 0) {  // invalid, or s == t: answered on the host
     sv->results[rq.ticket] = {P.status == PW_OK ? 0.0 : NAN, P.status, now_ms() - rq.t_submit_ms};
     sv->unfinished.erase(rq.ticket);
@@ -460,7 +476,7 @@ static bool admit(pw_server* sv, const Request& rq) {
   h.ps = (double*)(sv->d_pool + off + sizeof(double) * (size_t)P.K);
   if (!pilot) {
     const double visits = 2.0 * (double)P.R * (double)(P.L + 1);
-    const uint32_t words = (uint32_t)((sv->smem - sizeof(float) * kServerRmax) / sizeof(uint32_t));
+    const uint32_t words = (uint32_t)((sv->smem - kServerMeansBytes) / sizeof(uint32_t));
     h.use_table = (words > 0 && sv->table_probe_cost < sv->table_visit_gain * visits) ? 1u : 0u;
   }
   sv->h_comp[slot].ticket = 0;
@@ -560,7 +576,6 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
   BudgetArgs ba;
   pw_status st = resolve_budget(params, g, &ba, nullptr);
   if (st != PW_OK) return st;
-  if (ba.mode == PW_BUDGET_PILOT && ba.R_max > kServerRmax) ba.R_max = kServerRmax;
   if (ba.G > kServerGmax) return set_error(PW_ERR_ARG, "server supports G <= 2048");
   if (accum_bytes < ((size_t)1 << 20)) accum_bytes = (size_t)1 << 20;
   PW_CUDA_TRY(cudaSetDevice(g->device));
@@ -610,9 +625,9 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
   sv->slot_range.assign(sv->S, {0, 0});
   sv->slot_submit_ms.assign(sv->S, 0.0);
   for (uint32_t s = 0; s < sv->S; ++s) sv->free_slots.push_back(sv->S - 1 - s);
-  // shared memory: probe table (if it fits next to the U_p buffer) + U_p
-  const size_t ubytes = sizeof(float) * kServerRmax;
-  // rounded to 16 bytes so the U_p area that follows (reused for FP64 block means) stays aligned
+  // shared memory: probe table (if it fits next to the block means) + block means
+  const size_t ubytes = kServerMeansBytes;
+  // rounded to 16 bytes so the FP64 block means that follow stay aligned
   const size_t tbytes = (sizeof(uint32_t) * (size_t)table_words((uint32_t)g->n) + 15) & ~(size_t)15;
   sv->smem = ubytes + ((tbytes + ubytes <= 200 * 1024) ? tbytes : 0);
   const bool with_table = sv->smem > ubytes;

@@ -123,6 +123,7 @@ SIGNATURES = {
     "pw_debug_probe": (_i32, [_vp, _u64, _u32, _u32, P(ctypes.c_int8), P(_i32)]),
     "pw_debug_walk": (_i32, [_vp, _i64, _i32, _u64, _u64, _u32, P(_i64)]),
     "pw_debug_gather_peak": (_i32, [_vp, _i32, P(_dbl)]),
+    "pw_debug_exact_sum": (_i32, [_vp, P(ctypes.c_float), _i64, P(_dbl), P(_dbl)]),
     "pw_debug_query": (_i32, [_vp, _i64, _i64, _dbl, _i32, P(_u64), P(pw_params), P(_dbl), P(_u64), P(_dbl),
                               P(_dbl), _i64, P(ctypes.c_float), _i64, P(_u32)]),
     "pw_debug_batch_probe_q": (_i32, [_vp, _i64, P(_i64), P(_i64), P(_dbl), P(_i32), P(_u64), P(pw_params), P(_dbl),
@@ -384,6 +385,14 @@ def pw_debug_gather_peak(g: int, iters: int = 2048) -> float:
     out = _dbl()
     _check(lib().pw_debug_gather_peak(g, iters, ctypes.byref(out)))
     return out.value
+
+
+def pw_debug_exact_sum(g: int, u) -> tuple[float, float]:
+    """(S1, S2) of FP32 values through the device's exact per-probe accumulator."""
+    u = _arr(u, np.float32)
+    s1, s2 = _dbl(), _dbl()
+    _check(lib().pw_debug_exact_sum(g, _p(u, ctypes.c_float), u.size, ctypes.byref(s1), ctypes.byref(s2)))
+    return s1.value, s2.value
 
 
 def pw_debug_walk(g: int, start: int, L: int, seed: int, walk_id: int, tag: int = TAG_WALK) -> np.ndarray:

@@ -97,6 +97,74 @@ def test_trajectories_bit_exact(pw, oracle_lib, tiny):
                                       oracle.walk(host, start, L, seed, wid, tag))
 
 
+def test_device_exact_sums_match_oracle(pw, oracle_lib, tiny):
+    """The walk kernels' per-probe accumulator (exact integer digits, one
+    rounding) gives the oracle's S1 and S2 bit for bit, ties and near-ties
+    included, on values in the range every replica value lies in."""
+    _, g = tiny
+    e = 2.0**-53
+    cases = [[1.0, e], [1.0, 2 * e, e], [1.0, e, e], [e, e, 1.0], [-1.0, -e, -e], [3.0, -3.0], [],
+             [2.0**20, 2.0**-33, 2.0**-54], [2.0**20, 2.0**-33], [2.0**32, -1.0, 2.0**-54]]
+    for vals in cases:
+        u = np.array(vals, np.float32)
+        got = pw.pw_debug_exact_sum(g.handle, u)
+        want = (oracle.exact_sum_f32(u), oracle.exact_sum_f32(u, square=True))
+        assert got == want, (vals, got, want)
+    rng = np.random.default_rng(23)
+    for trial in range(12):
+        n = int(rng.integers(1, 5000))
+        u = (rng.standard_normal(n) * 2.0 ** rng.integers(-25, 12, size=n)).astype(np.float32)
+        if trial % 2:
+            u = np.concatenate([u, -u[: n // 2]])
+        got = pw.pw_debug_exact_sum(g.handle, u)
+        assert got == (oracle.exact_sum_f32(u), oracle.exact_sum_f32(u, square=True))
+
+
+def test_mixed_walk_kernels_in_one_batch(pw, oracle_lib, tiny):
+    """The walk kernel is chosen per query on the device: with L = 0 the table
+    does not pay (2 R visits per probe against n Feistel passes), with longer
+    walks it does, so one batch runs both kernels; every estimate equals the
+    oracle's and the forced single-kernel runs'."""
+    host, g = tiny
+    s, t = uniform_pairs(host.n, 20, 420)
+    seeds = query_seeds(20, 421)
+    L = np.where(np.arange(20) % 2 == 0, 0, 24).astype(np.int32)
+    pw.pw_profile(g.handle, enable=True, reset=True)
+    auto, st = pw.pw_query_batch(g.handle, s, t, 0.25, L, seeds)
+    assert pw.pw_profile(g.handle, enable=False, reset=True)["walk_mode"] == 3
+    assert np.all(st == 0)
+    want, _, ost = oracle.query_many(host, s, t, 0.25, L, seeds)
+    np.testing.assert_allclose(auto, want, rtol=REL_TOL, atol=0)
+    np.testing.assert_array_equal(auto, want)
+    for mode in (1, 2):
+        forced, _ = pw.pw_query_batch(g.handle, s, t, 0.25, L, seeds, pw.make_params(walk_mode=mode))
+        np.testing.assert_array_equal(forced, want)
+
+
+def test_repeated_calls_replay_a_cuda_graph(pw, oracle_lib, tiny):
+    """A host-array call runs eagerly the first time its shape is seen, is
+    captured as a CUDA graph the second time and replayed afterwards: every
+    call gives the oracle's estimates and counts the same kernel launches."""
+    host, g = tiny
+    s, t = uniform_pairs(host.n, 6, 430)
+    seeds = query_seeds(6, 431)
+    want, _, _ = oracle.query_many(host, s, t, 0.2, 32, seeds)
+    counts = []
+    for i in range(6):
+        pw.pw_launch_count(reset=True)
+        assert pw.pw_query(g.handle, int(s[i]), int(t[i]), 0.2, 32, int(seeds[i])) == want[i]
+        counts.append(pw.pw_launch_count(reset=True))
+    assert len(set(counts)) == 1 and counts[0] > 0
+    for _ in range(3):
+        b, st = pw.pw_query_batch(g.handle, s, t, 0.2, 32, seeds)
+        assert np.all(st == 0)
+        np.testing.assert_array_equal(b, want)
+    b, _ = pw.pw_query_batch(g.handle, s[:4], t[:4], 0.2, 32, seeds[:4])  # another shape
+    np.testing.assert_array_equal(b, want[:4])
+    b, _ = pw.pw_query_batch(g.handle, s, t, 0.2, 32, seeds)
+    np.testing.assert_array_equal(b, want)
+
+
 def _compare_query(pw, host, g, s, t, eps, L, seed, params, cfg):
     dev = pw.pw_debug_query(g.handle, host.n, s, t, eps, L, seed, params, q_cap=1 << 22, u_cap=1 << 26,
                             want_visits=True)
