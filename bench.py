@@ -358,6 +358,54 @@ def run_eps_sweep(args, wl, world, rank, local):
     g.close()
 
 
+def run_accuracy(args, wl, world, rank, local):
+    """Problem 1's target on the workload: the fraction of queries whose
+    estimate is within eps of beta^(L) (pw_series_batch, FP64-accurate to
+    1e-9), at eps = 0.1 and 0.2 and each R_max of --r-max, with the walk
+    transitions and the wall time each setting costs."""
+    import torch
+
+    from paper_2512_05460_gb300 import build as pwbuild
+
+    pwbuild.build()
+    from paper_2512_05460_gb300 import probewalk as pw
+
+    torch.cuda.set_device(local)
+    from pw_inputs import query_seeds, uniform_pairs, workload_graph
+
+    n = args.queries or 256
+    host = workload_graph(wl["graph"])
+    s, t = uniform_pairs(host.n, n, wl["pair_seed"] + 7919 * rank)
+    seeds = query_seeds(n, wl["seed_seed"] + 7919 * rank)
+    L = wl["L"]
+    g = pw.Graph(host.row_ptr, host.col_idx, device=local)
+    ref = pw.pw_series_batch(g.handle, s, t, np.full(n, L, np.int32))
+    rows = []
+    settings = [(float(c), int(r)) for c in args.c_B_list.split(",") for r in args.r_max.split(",")]
+    for e in (0.1, 0.2):
+        for cb, rmax in settings:
+            params = pw.make_params(R_max=rmax, c_B=cb)
+            pw.pw_profile(g.handle, enable=True, reset=True)
+            t0 = time.perf_counter()
+            beta, st, KR, _ = pw.pw_debug_batch_probe_q(g.handle, s, t, e, L, seeds, [], [], params)
+            wall = time.perf_counter() - t0
+            prof = pw.pw_profile(g.handle, enable=False, reset=True)
+            assert np.all(st == 0)
+            rel = np.abs(beta - ref) / ref
+            clamped = KR[:, 1] == rmax
+            rows.append({"eps": e, "c_B": cb, "R_max": rmax, "frac_within_eps": float(np.mean(rel <= e)),
+                         "frac_clamped": float(np.mean(clamped)),
+                         "frac_within_eps_clamped": float(np.mean(rel[clamped] <= e)) if clamped.any() else None,
+                         "frac_within_eps_unclamped": float(np.mean(rel[~clamped] <= e)) if (~clamped).any() else None,
+                         "transitions": int(prof["transitions"]), "walk_s": prof["walk_ms"] / 1000.0, "wall_s": wall})
+    line = {"metric": "fraction of queries within eps of beta^(L) (Problem 1) and its cost, by R_max",
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}; {n} uniform pairs; L={L}; PILOT budget; "
+                                   "reference beta^(L) from pw_series_batch"}, "rows": rows}
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
 def run_series(args, wl, world, rank, local):
     """The deterministic truncated series beta^(L) (Lemma 2.3) on the GPU
     (pw_series_batch, double-float steps, 32 queries per pass): queries/s and
@@ -480,7 +528,7 @@ def run_ours(args, wl, world, rank, local):
     nq = s.size
     eps = workload_eps(wl, nq, rank)
     L = np.full(nq, wl["L"], np.int32)
-    g = pw.Graph(host.row_ptr, host.col_idx, device=local)
+    g = pw.Graph(host.row_ptr, host.col_idx, device=local, flags={0: 0, 1: pw.LOAD_FUSED, 2: pw.LOAD_SPLIT}[args.layout])
     params = pw.make_params(c_B=args.c_B, walk_mode=args.walk_mode)
     d_s = torch.from_numpy(s).to(dev)
     d_t = torch.from_numpy(t).to(dev)
@@ -587,17 +635,20 @@ def run_ours(args, wl, world, rank, local):
         server = run_server(pw, g, s, t, eps, L, seeds, params, beta)
 
     # ---- roofline of the walk kernel -----------------------------------------
-    # Algorithmic bytes: one 32-byte sector (holding the 16-byte neighbour
-    # record) per walk transition.  Records larger than L2 are bound by HBM
-    # (MEASURED_PEAKS.json); an L2-resident record array (this BA graph: 16 MB)
-    # is bound by L2 sector throughput, measured here by dependent random
-    # gathers over the same array.
+    # Algorithmic bytes per walk transition: one 32-byte sector per gather, one
+    # gather (the 16-byte fused neighbour record) or two (a col_idx entry, then
+    # the neighbour's 16-byte node record) by the graph's layout.  Arrays larger
+    # than L2 are bound by HBM (MEASURED_PEAKS.json); L2-resident ones (this BA
+    # graph: 16 MB of records) by L2 sector throughput, measured here by
+    # dependent random gathers with the same access.
     hbm_peak, peak_kind = load_peaks()
-    walk_bytes = transitions_per_step * SECTOR_BYTES
+    layout = prof.get("layout", 1)
+    gathers = 1 if layout == 1 else 2
+    walk_bytes = transitions_per_step * SECTOR_BYTES * gathers
     achieved = walk_bytes / (walk_ms_avg / 1000.0) / 1e9 if walk_ms_avg > 0 else 0.0
-    record_bytes = 16 * host.nnz
+    record_bytes = 16 * host.nnz if layout == 1 else 4 * host.nnz + 16 * host.n
     if record_bytes < L2_BYTES // 2:
-        l2_peak = pw.pw_debug_gather_peak(g.handle, 2048) * SECTOR_BYTES / 1e9
+        l2_peak = pw.pw_debug_gather_peak(g.handle, 2048) * SECTOR_BYTES * gathers / 1e9
         roofline = {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
                     "peak_kind": "measured in this run: dependent random 16-B gathers over the same record array "
                                  "(pw_debug_gather_peak)"}
@@ -605,7 +656,7 @@ def run_ours(args, wl, world, rank, local):
         # Context beside the copy peak: the ceiling of this access pattern
         # (dependent random 16-B gathers, uniform over the same records, which
         # is where a stationary walk's transitions land), measured in this run.
-        gather = pw.pw_debug_gather_peak(g.handle, 512) * SECTOR_BYTES / 1e9
+        gather = pw.pw_debug_gather_peak(g.handle, 512) * SECTOR_BYTES * gathers / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                     "gather_ceiling": gather, "frac_of_gather_ceiling": achieved / gather,
@@ -617,7 +668,10 @@ def run_ours(args, wl, world, rank, local):
                      "traffic_note": tr and tr["note"],
                      "kernel": WALK_KERNEL_NAME[walk_mode],
                      "algorithmic_bytes_per_launch": walk_bytes,
-                     "bytes_model": "32 B (one sector holding the 16 B neighbour record) per walk transition",
+                     "layout": {1: "fused 16-B neighbour records", 2: "col_idx + 16-B node records"}[layout],
+                     "bytes_model": ("32 B (one sector holding the 16 B neighbour record) per walk transition"
+                                     if layout == 1 else "64 B per walk transition: the sector holding the 4 B "
+                                                         "col_idx entry and the sector holding the 16 B node record"),
                      "walk_ms_per_launch": walk_ms_avg})
 
     cpu = None
@@ -686,9 +740,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-server", action="store_true")
     ap.add_argument("--no-tiny", action="store_true", help="skip the tiny-graph batched-vs-plain comparison")
+    ap.add_argument("--layout", type=int, default=0, choices=[0, 1, 2],
+                    help="walk layout: 0 by size, 1 fused records, 2 col_idx + node records")
     ap.add_argument("--stabilized", action="store_true", help="L by the stabilization rule (Section 4.3)")
     ap.add_argument("--eps-sweep", action="store_true", help="runtime and error over eps (Fig. 2 protocol)")
     ap.add_argument("--series", action="store_true", help="the GPU truncated series beta^(L) (Lemma 2.3)")
+    ap.add_argument("--accuracy", action="store_true", help="fraction within eps of beta^(L), by R_max")
+    ap.add_argument("--r-max", default="4096,8192,16384", help="R_max values of --accuracy")
+    ap.add_argument("--c-B-list", default="0.5", help="c_B values of --accuracy")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -700,6 +759,8 @@ def main():
         run_stabilized(args, wl, world, rank, local)
     elif args.series:
         run_series(args, wl, world, rank, local)
+    elif args.accuracy:
+        run_accuracy(args, wl, world, rank, local)
     elif args.eps_sweep:
         run_eps_sweep(args, wl, world, rank, local)
     else:

@@ -89,7 +89,12 @@ typedef struct pw_server pw_server;
  * edge present in both directions, every node of degree >= 1, the graph
  * connected (Section 2.1).  Requires 2 <= n < 2^31 and nnz < 2^31.  The arrays
  * are copied; the caller keeps ownership.  flags: bit 0 skips the O(n + m)
- * connectivity check.  Returns PW_ERR_GRAPH if a check fails.
+ * connectivity check; bits 1 and 2 force the walks' graph layout, fused
+ * 16-byte neighbour records (bit 1: one gather per walk step) or col_idx plus
+ * 16-byte node records (bit 2: two smaller gathers per step); by default the
+ * fused records are built when they take at most 64 MiB (half of the L2), and
+ * the split layout is used otherwise.  Both give the same walks.  Returns
+ * PW_ERR_GRAPH if a check fails.
  * On success *out holds a handle to free with pw_graph_free. */
 pw_status pw_graph_load(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz,
                         int32_t device, uint32_t flags, pw_graph** out);
@@ -270,11 +275,13 @@ pw_status pw_debug_philox(pw_graph* g, const uint32_t* ctr, const uint32_t* key,
  * n) of probe k under stream tag `tag` (3 main, 4 pilot) of the query keyed by
  * seed; returns the parity parameter r in *r (host, may be NULL). */
 pw_status pw_debug_probe(pw_graph* g, uint64_t seed, uint32_t k, uint32_t tag, int8_t* z, int32_t* r);
-/* pw_debug_gather_peak: sector-throughput ceiling of the walk's memory side on
- * this graph: dependent random 16-byte gathers over the graph's record array
- * (8 chains per thread, full occupancy, no other work), best of 3 launches of
- * `iters` gathers per chain; *sectors_per_s (host) receives gathers/s, each
- * gather reading one 32-byte sector. */
+/* pw_debug_gather_peak: throughput ceiling of the walk's memory side on this
+ * graph: dependent random gathers with the walk's access per step (fused
+ * layout: one 16-byte record uniform over the record array; split layout: one
+ * col_idx entry uniform over col_idx, then the node record it names), 8 chains
+ * per thread, full occupancy, no other work, best of 3 launches of `iters`
+ * steps per chain.  *sectors_per_s (host) receives steps/s (each step reads one
+ * 32-byte sector per gather). */
 pw_status pw_debug_gather_peak(pw_graph* g, int32_t iters, double* sectors_per_s);
 /* pw_debug_walk: trajectory X_0..X_L (host int64 array of L+1) of walk
  * `walk_id` under stream tag `tag` (1 main, 2 pilot). */
@@ -318,7 +325,7 @@ typedef struct pw_profile_stats {
   uint64_t pilot_transitions;
   uint64_t queries;
   int32_t walk_mode;           /* walk kernels of the last batch: 1 per-visit probe evaluation, 2 probe table, 3 both */
-  int32_t reserved;
+  int32_t layout;              /* the graph's walk layout: 1 fused records, 2 col_idx + node records */
   double series_ms;            /* pw_series_batch passes (32 queries each), summed */
   uint64_t series_steps;       /* sparse steps of those passes: L + 1 per pass */
 } pw_profile_stats;
@@ -329,10 +336,15 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
  * give bit-identical results, so the choice only changes speed.
  *
  * Runs the caller's sample batch (host arrays as in pw_query_batch, seeds may
- * be NULL) three times through the walk kernels, each after one untimed
- * warm-up: per-visit probe evaluation at the given L, and the per-probe
- * shared-memory table at L and at L/4 (4 L where L < 4).  From the main walk
- * kernel's CUDA-event time of each run it fits
+ * be NULL, each query's s, t, L) with a FIXED budget of B = 4 probes per
+ * block, params' G, and R = 1024 replicas, each run after one untimed
+ * warm-up: the per-visit kernel in its two register variants (compiler's
+ * choice, or capped for 3 blocks of 256 per SM), keeping the faster; the
+ * per-probe shared-memory table with blocks of 256, 512 and 1024 threads,
+ * keeping the fastest; and that table kernel again at R = 256 (the same
+ * probes, a quarter of the visits).  The kept variants are stored in the
+ * graph and used by every later batch.  From the main walk kernels'
+ * CUDA-event time of the kept runs it fits
  *   per-visit:  t = visits * visit_ns
  *   table:      t = probes * table_probe_ns + visits * table_visit_ns
  * (visits = 2 K R (L+1) summed over the batch) and stores the costs in the
@@ -350,9 +362,11 @@ typedef struct pw_tune_result {
   double visit_ns;         /* per-visit kernel, ns per visit */
   double table_visit_ns;   /* table kernel, ns per visit (0 when unavailable) */
   double table_probe_ns;   /* table kernel, ns per probe for the table build (0 when unavailable) */
-  double sample_ms[3];     /* walk-kernel time of each timed run (per-visit; table at L; table at L/4) */
+  double sample_ms[3];     /* walk-kernel time of the kept runs (per-visit; table at R = 1024; table at R = 256) */
   int32_t table_available; /* 1 when the probe table fits in shared memory */
   int32_t sample_mode;     /* walk kernel the fitted model picks for the sample: 1 per-visit, 2 table */
+  int32_t visit_occupancy; /* per-visit kernel variant kept: 1 compiler-chosen registers, 3 capped for 3 blocks/SM */
+  int32_t table_threads;   /* table-kernel block size kept: 256, 512 or 1024 (0 when unavailable) */
 } pw_tune_result;
 pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
                       const int32_t* L, const uint64_t* seeds, const pw_params* params, pw_tune_result* out);

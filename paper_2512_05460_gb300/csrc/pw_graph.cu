@@ -12,11 +12,13 @@
 
 namespace pw {
 
-// rec[e] = {u, row_start(u), deg(u), bits(1/deg(u))} for every CSR entry e; node[v] likewise for v.
+// node[v] = {v, row_start(v), deg(v), bits(1/deg(v))}; in the fused layout
+// also rec[e] = node[col[e]] for every CSR entry e (rec may be NULL).
 __global__ void build_records_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                      int64_t n, int64_t nnz, int4* __restrict__ rec, int4* __restrict__ node) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz + n; e += stride) {
+  const int64_t first = rec ? 0 : nnz;
+  for (int64_t e = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz + n; e += stride) {
     const int32_t u = e < nnz ? col[e] : (int32_t)(e - nnz);
     const int32_t start = row_ptr[u];
     const int32_t d = row_ptr[u + 1] - start;
@@ -44,7 +46,7 @@ __global__ void debug_probe_kernel(uint32_t n, uint64_t seed, uint32_t k, uint32
 // One trajectory with the walk kernel's step rule: step i draws word (i & 3) of
 // the Philox block (walk lo, walk hi, i >> 2, tag) and moves to neighbour
 // floor(word * d / 2^32).
-__global__ void debug_walk_kernel(const int4* __restrict__ rec, const int4* __restrict__ node, int32_t start,
+__global__ void debug_walk_kernel(const int32_t* __restrict__ col, const int4* __restrict__ node, int32_t start,
                                   int32_t L, uint64_t seed, uint64_t walk_id, uint32_t tag, int64_t* traj) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   int4 cur = node[start];
@@ -53,15 +55,19 @@ __global__ void debug_walk_kernel(const int4* __restrict__ rec, const int4* __re
     const Philox4 o = philox_seeded(seed, (uint32_t)walk_id, (uint32_t)(walk_id >> 32), (uint32_t)i >> 2, tag);
     const uint32_t w[4] = {o.x, o.y, o.z, o.w};
     const uint32_t j = __umulhi(w[i & 3], (uint32_t)cur.z);
-    cur = rec[(uint32_t)cur.y + j];
+    cur = node[col[(uint32_t)cur.y + j]];
     traj[i] = cur.x;
   }
 }
 
-// Sector-throughput ceiling of the walk's memory side: dependent random 16-B
-// gathers over the graph's own record array (the next index depends on the
+// Sector-throughput ceiling of the walk's memory side: dependent random
+// gathers with the walk's access per step (the next index depends on the
 // loaded value, as in a walk), 8 independent chains per thread, no other work.
-__global__ void __launch_bounds__(256) gather_peak_kernel(const int4* __restrict__ rec, uint32_t nnz, uint32_t iters,
+// Fused layout: one 16-B record uniform over the record array.  Split layout:
+// a 4-B col_idx entry uniform over col_idx, then the node record it names.
+template <bool SPLIT>
+__global__ void __launch_bounds__(256) gather_peak_kernel(const int4* __restrict__ rec, const int32_t* __restrict__ col,
+                                                         const int4* __restrict__ node, uint32_t nnz, uint32_t iters,
                                                          uint32_t* sink) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t x[8];
@@ -71,7 +77,8 @@ __global__ void __launch_bounds__(256) gather_peak_kernel(const int4* __restrict
   for (uint32_t it = 0; it < iters; ++it) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int4 r = __ldg(rec + __umulhi(x[j], nnz));
+      const uint32_t e = __umulhi(x[j], nnz);
+      const int4 r = SPLIT ? __ldg(node + __ldg(col + e)) : __ldg(rec + e);
       x[j] = x[j] * 1664525u + 1013904223u + (uint32_t)r.y;
       acc += (uint32_t)r.x;
     }
@@ -162,7 +169,8 @@ static pw_status upload(pw_graph* g, const int64_t* rp64, const int32_t* col) {
   int32_t *d_rp = nullptr, *d_col = nullptr;
   PW_CUDA_TRY(cudaMalloc(&d_rp, sizeof(int32_t) * (size_t)(g->n + 1)));
   PW_CUDA_TRY(cudaMalloc(&d_col, sizeof(int32_t) * (size_t)g->nnz));
-  PW_CUDA_TRY(cudaMalloc(&g->d_rec, sizeof(int4) * (size_t)g->nnz));
+  g->d_col = d_col;
+  if (g->layout == 1) PW_CUDA_TRY(cudaMalloc(&g->d_rec, sizeof(int4) * (size_t)g->nnz));
   PW_CUDA_TRY(cudaMalloc(&g->d_node, sizeof(int4) * (size_t)g->n));
   PW_CUDA_TRY(cudaMemcpyAsync(d_rp, rp32.data(), sizeof(int32_t) * (size_t)(g->n + 1), cudaMemcpyHostToDevice,
                               g->stream));
@@ -175,7 +183,6 @@ static pw_status upload(pw_graph* g, const int64_t* rp64, const int32_t* col) {
   PW_CUDA_TRY(cudaGetLastError());
   PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
   cudaFree(d_rp);
-  cudaFree(d_col);
   PW_CUDA_TRY(cudaMallocHost(&g->ws.host_totals, sizeof(Totals)));
   PW_CUDA_TRY(cudaEventCreateWithFlags(&g->ws.last_use, cudaEventDisableTiming));
   return PW_OK;
@@ -195,6 +202,7 @@ static void destroy(pw_graph* g) {
   for (pw::Totals* h : g->prof.pending) cudaFreeHost(h);
   for (pw::Totals* h : g->prof.spare) cudaFreeHost(h);
   if (g->d_rec) cudaFree(g->d_rec);
+  if (g->d_col) cudaFree(g->d_col);
   if (g->d_node) cudaFree(g->d_node);
   if (g->stream) cudaStreamDestroy(g->stream);
   delete g;
@@ -219,6 +227,14 @@ static pw_status load_common(int64_t n, const int64_t* rp, const int32_t* col, i
   g->d_min = dmn;
   g->d_max = dmx;
   g->bipartite = bip;
+  // walk layout: fused 16-byte records while they fill at most half of the L2
+  // (64 MiB), else col_idx plus node records (flags bit 1 / bit 2 force one)
+  if (flags & 2u)
+    g->layout = 1;
+  else if (flags & 4u)
+    g->layout = 2;
+  else
+    g->layout = 16.0 * (double)nnz <= (double)((size_t)64 << 20) ? 1 : 2;
   st = upload(g, rp, col);
   if (st != PW_OK) {
     destroy(g);
@@ -302,7 +318,9 @@ pw_status pw_debug_gather_peak(pw_graph* g, int32_t iters, double* sectors_per_s
   pw_status st = pw::ensure_buffer(b, 64);
   if (st != PW_OK) return st;
   int nb = 0;
-  PW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pw::gather_peak_kernel, 256, 0));
+  const bool split = g->layout == 2;
+  PW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &nb, split ? pw::gather_peak_kernel<true> : pw::gather_peak_kernel<false>, 256, 0));
   const int blocks = g->sm_count * (nb > 0 ? nb : 1);
   cudaEvent_t e0, e1;
   PW_CUDA_TRY(cudaEventCreate(&e0));
@@ -310,8 +328,12 @@ pw_status pw_debug_gather_peak(pw_graph* g, int32_t iters, double* sectors_per_s
   double best = 0.0;
   for (int rep = 0; rep < 3; ++rep) {
     PW_CUDA_TRY(cudaEventRecord(e0, g->stream));
-    pw::gather_peak_kernel<<<blocks, 256, 0, g->stream>>>(g->d_rec, (uint32_t)g->nnz, (uint32_t)iters,
-                                                          (uint32_t*)b.ptr);
+    if (split)
+      pw::gather_peak_kernel<true><<<blocks, 256, 0, g->stream>>>(g->d_rec, g->d_col, g->d_node, (uint32_t)g->nnz,
+                                                                  (uint32_t)iters, (uint32_t*)b.ptr);
+    else
+      pw::gather_peak_kernel<false><<<blocks, 256, 0, g->stream>>>(g->d_rec, g->d_col, g->d_node, (uint32_t)g->nnz,
+                                                                   (uint32_t)iters, (uint32_t*)b.ptr);
     pw::count_launch();
     PW_CUDA_TRY(cudaGetLastError());
     PW_CUDA_TRY(cudaEventRecord(e1, g->stream));
@@ -336,7 +358,7 @@ pw_status pw_debug_walk(pw_graph* g, int64_t start, int32_t L, uint64_t seed, ui
   pw::DeviceBuffer& b = g->ws.results;
   pw_status st = pw::ensure_buffer(b, sizeof(int64_t) * ((size_t)L + 1));
   if (st != PW_OK) return st;
-  pw::debug_walk_kernel<<<1, 32, 0, g->stream>>>(g->d_rec, g->d_node, (int32_t)start, L, seed, walk_id, tag,
+  pw::debug_walk_kernel<<<1, 32, 0, g->stream>>>(g->d_col, g->d_node, (int32_t)start, L, seed, walk_id, tag,
                                                  (int64_t*)b.ptr);
   pw::count_launch();
   PW_CUDA_TRY(cudaGetLastError());

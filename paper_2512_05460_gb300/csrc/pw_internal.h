@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -105,10 +106,17 @@ struct pw_graph {
   // pw_autotune replaces them by nanoseconds measured on this graph.
   double table_probe_cost = 0.0, table_visit_gain = 2.5;
   int tuned = 0;
-  int4* d_rec = nullptr;   // nnz neighbour records
-  int4* d_node = nullptr;  // n node records
+  int4* d_rec = nullptr;     // nnz neighbour records (fused layout only)
+  int32_t* d_col = nullptr;  // nnz neighbour ids (always)
+  int4* d_node = nullptr;    // n node records
+  int layout = 1;            // walk access: 1 fused records, 2 col_idx + node records
   cudaStream_t stream = nullptr;
-  int table_grid[2] = {0, 0};  // grid of the table kernel (plain, debug), fixed by n
+  std::map<std::pair<const void*, size_t>, int> grids;  // persistent grid per walk kernel and shared memory
+  // Kernel variants (pw_autotune): per-visit kernel with compiler-chosen
+  // registers (1) or registers capped for 3 blocks per SM (3); table-kernel
+  // block size (0: by shared memory, else 256, 512 or 1024 threads).
+  int visit_minb = 1;
+  int table_threads = 0;
   std::mutex lock;
   pw::GraphCache gcache;
   pw::Workspace ws;

@@ -189,7 +189,8 @@ __device__ __forceinline__ int64_t find_segment(const unsigned long long* __rest
 }
 
 struct WalkArgs {
-  const int4* rec;
+  const int4* rec;   // fused records (layout 1)
+  const int32_t* col;  // col_idx (layout 2)
   const int4* node;
   const QPlan* plans;
   const unsigned long long* tile_prefix;   // per-visit tiles
@@ -211,8 +212,24 @@ struct WalkArgs {
 // its tile's replicas exactly; a pilot tile is a whole probe (R0 <= 32) and
 // writes (S1, S2); a main tile adds its digits to the probe's accumulator and
 // the probe's last tile computes Q_R.
-template <bool DEBUG, bool PILOT>
-__global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkArgs A) {
+// The graph access of a launch: fused records, or col_idx plus node records.
+template <bool SPLIT>
+struct GraphOf;
+template <>
+struct GraphOf<false> {
+  static __device__ __forceinline__ FusedRecords get(const WalkArgs& A) { return FusedRecords{A.rec, A.node}; }
+};
+template <>
+struct GraphOf<true> {
+  static __device__ __forceinline__ SplitRecords get(const WalkArgs& A) { return SplitRecords{A.col, A.node}; }
+};
+
+// MINB: 1 leaves the registers to the compiler (2 blocks of 256 per SM), 3
+// caps them for 3 blocks per SM (more walks in flight, some spills); the
+// autotuner picks one per graph.
+template <bool DEBUG, bool PILOT, bool SPLIT, int MINB>
+__global__ void __launch_bounds__(kWalkThreads, MINB) walk_kernel(WalkArgs A) {
+  const auto gr = GraphOf<SPLIT>::get(A);
   const uint32_t lane = threadIdx.x & 31u;
   const unsigned long long total = A.totals->tiles;
   for (;;) {
@@ -234,7 +251,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkArgs A) {
       const Probe pr = make_probe(A.n, P.seed, k, A.probe_tag);
       const uint64_t pair = (uint64_t)k * R + p;
       const ZOnTheFly zp{pr};
-      const float U = walk_pair<DEBUG>(A.rec, A.node, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
+      const float U = walk_pair<DEBUG>(gr, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
       if (DEBUG && A.u_debug && q == 0) A.u_debug[(uint64_t)kl * R + p] = U;
       sum_add(sum, U);
     }
@@ -269,8 +286,11 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkArgs A) {
 // digits, and the block writes the probe's Q_R.  Same values as the per-visit
 // kernel; cheaper whenever a probe's walks visit more nodes than the Feistel
 // domain has (2 R (L+1) > 2^b).
-template <bool DEBUG>
-__global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A) {
+// THREADS: 256 (five blocks per SM for small tables), 512 or 1024 (one or two
+// blocks per SM with up to 200 KB of table, still 32 warps).
+template <bool DEBUG, bool SPLIT, int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : (THREADS == 512 ? 2 : 1)) walk_table_kernel(WalkArgs A) {
+  const auto gr = GraphOf<SPLIT>::get(A);
   extern __shared__ uint32_t tab[];
   __shared__ unsigned long long sh_probe;
   __shared__ unsigned long long sh_sum[kSumDigits];
@@ -305,7 +325,7 @@ __global__ void __launch_bounds__(kWalkThreads, 5) walk_table_kernel(WalkArgs A)
       sum_clear(sum);
       if (p < R) {
         const uint64_t pair = (uint64_t)k * R + p;
-        const float U = walk_pair_table<DEBUG>(A.rec, A.node, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
+        const float U = walk_pair_table<DEBUG>(gr, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
         if (DEBUG && A.u_debug && q == 0) A.u_debug[(uint64_t)kl * R + p] = U;
         sum_add(sum, U);
       }
@@ -414,17 +434,6 @@ __global__ void block_means_kernel(const QPlan* __restrict__ plans, const double
   if (threadIdx.x == 0) status[0] = P.status;
 }
 
-template <bool DEBUG, bool PILOT>
-static int walk_grid(pw_graph* g) {
-  static int occ = 0;
-  if (occ == 0) {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<DEBUG, PILOT>, kWalkThreads, 0);
-    occ = nb > 0 ? nb : 1;
-  }
-  return g->sm_count * occ;
-}
-
 static cudaEvent_t prof_event(pw_graph* g) {
   ProfileState& P = g->prof;
   if (!P.pool.empty()) {
@@ -455,30 +464,66 @@ void prof_end(pw_graph* g, cudaStream_t stream, cudaEvent_t a, int kind) {
 static size_t table_bytes(const pw_graph* g) { return sizeof(uint32_t) * (size_t)table_words((uint32_t)g->n); }
 static constexpr size_t kMaxTableBytes = 200 * 1024;
 
-template <bool DEBUG>
-static int table_grid(pw_graph* g, size_t smem) {
-  int& grid = g->table_grid[DEBUG ? 1 : 0];
-  if (grid == 0) {
-    int nb = 0;
-    cudaFuncSetAttribute(walk_table_kernel<DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_table_kernel<DEBUG>, kWalkThreads, smem);
-    grid = g->sm_count * (nb > 0 ? nb : 1);
+// Table-kernel block size by shared memory: 256 threads while five tables fit
+// per SM (then registers limit it to five blocks), 512 while two fit, else 1024.
+static int default_table_threads(const pw_graph* g) {
+  const size_t per_block = table_bytes(g) + 2048;
+  const size_t fit = ((size_t)228 << 10) / per_block;
+  return fit >= 5 ? 256 : (fit >= 2 ? 512 : 1024);
+}
+
+using WalkFn = void (*)(WalkArgs);
+
+// The per-visit kernel of a launch (DEBUG builds exist only at MINB 1).
+static WalkFn walk_fn(bool debug, bool pilot, bool split, int minb) {
+  if (debug) return split ? walk_kernel<true, false, true, 1> : walk_kernel<true, false, false, 1>;
+  if (minb == 3) {
+    if (pilot) return split ? walk_kernel<false, true, true, 3> : walk_kernel<false, true, false, 3>;
+    return split ? walk_kernel<false, false, true, 3> : walk_kernel<false, false, false, 3>;
   }
+  if (pilot) return split ? walk_kernel<false, true, true, 1> : walk_kernel<false, true, false, 1>;
+  return split ? walk_kernel<false, false, true, 1> : walk_kernel<false, false, false, 1>;
+}
+
+// The table kernel of a launch (DEBUG builds exist only at 256 threads).
+static WalkFn table_fn(bool debug, bool split, int threads) {
+  if (debug) return split ? walk_table_kernel<true, true, 256> : walk_table_kernel<true, false, 256>;
+  if (threads == 1024) return split ? walk_table_kernel<false, true, 1024> : walk_table_kernel<false, false, 1024>;
+  if (threads == 512) return split ? walk_table_kernel<false, true, 512> : walk_table_kernel<false, false, 512>;
+  return split ? walk_table_kernel<false, true, 256> : walk_table_kernel<false, false, 256>;
+}
+
+// Persistent grid: SMs x resident blocks, measured once per kernel and
+// shared-memory size on this graph.
+static int grid_of(pw_graph* g, WalkFn fn, int threads, size_t smem) {
+  const auto key = std::make_pair((const void*)fn, smem);
+  auto it = g->grids.find(key);
+  if (it != g->grids.end()) return it->second;
+  int nb = 0;
+  if (smem > 48 * 1024) cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, threads, smem);
+  const int grid = g->sm_count * (nb > 0 ? nb : 1);
+  g->grids[key] = grid;
   return grid;
 }
 
-template <bool DEBUG, bool PILOT>
-static pw_status launch_walk(pw_graph* g, cudaStream_t stream, const WalkArgs& a) {
-  walk_kernel<DEBUG, PILOT><<<walk_grid<DEBUG, PILOT>(g), kWalkThreads, 0, stream>>>(a);
+static pw_status launch_walk(pw_graph* g, cudaStream_t stream, const WalkArgs& a, bool debug, bool pilot) {
+  const WalkFn fn = walk_fn(debug, pilot, g->layout == 2, g->visit_minb);
+  fn<<<grid_of(g, fn, kWalkThreads, 0), kWalkThreads, 0, stream>>>(a);
   count_launch();
   PW_CUDA_TRY(cudaGetLastError());
   return PW_OK;
 }
 
-template <bool DEBUG>
-static pw_status launch_table(pw_graph* g, cudaStream_t stream, const WalkArgs& a) {
+static int table_threads(const pw_graph* g) {
+  return g->table_threads ? g->table_threads : default_table_threads(g);
+}
+
+static pw_status launch_table(pw_graph* g, cudaStream_t stream, const WalkArgs& a, bool debug) {
   const size_t smem = table_bytes(g);
-  walk_table_kernel<DEBUG><<<table_grid<DEBUG>(g, smem), kWalkThreads, smem, stream>>>(a);
+  const int threads = debug ? 256 : table_threads(g);
+  const WalkFn fn = table_fn(debug, g->layout == 2, threads);
+  fn<<<grid_of(g, fn, threads, smem), threads, smem, stream>>>(a);
   count_launch();
   PW_CUDA_TRY(cudaGetLastError());
   return PW_OK;
@@ -542,6 +587,7 @@ static pw_status enqueue_walks(pw_graph* g, int64_t count, const pw_params* para
   WalkArgs wa;
   memset(&wa, 0, sizeof wa);
   wa.rec = g->d_rec;
+  wa.col = g->d_col;
   wa.node = g->d_node;
   wa.nq = count;
   wa.n = (uint32_t)g->n;
@@ -559,7 +605,7 @@ static pw_status enqueue_walks(pw_graph* g, int64_t count, const pw_params* para
     wa.probe_tag = kTagProbePilot;
     cudaEvent_t ev;
     prof_begin(g, stream, &ev);
-    if ((st = launch_walk<false, true>(g, stream, wa)) != PW_OK) return st;
+    if ((st = launch_walk(g, stream, wa, false, true)) != PW_OK) return st;
     prof_end(g, stream, ev, 1);
     if (g->prof.enabled) g->prof.pilot_transitions += 2ull * nq * (uint64_t)ba.K0 * (uint64_t)ba.R0;
     pilot_budget_kernel<<<qblocks, qthreads, 0, stream>>>(count, B.plans, B.pplans, B.pilot_s, ba, g->d_node);
@@ -609,11 +655,11 @@ static pw_status enqueue_walks(pw_graph* g, int64_t count, const pw_params* para
   st = PW_OK;
   if (table_ok) {
     wa.counter = B.counters + 2;
-    st = debug ? launch_table<true>(g, stream, wa) : launch_table<false>(g, stream, wa);
+    st = launch_table(g, stream, wa, debug);
   }
   if (st == PW_OK) {
     wa.counter = B.counters;
-    st = debug ? launch_walk<true, false>(g, stream, wa) : launch_walk<false, false>(g, stream, wa);
+    st = launch_walk(g, stream, wa, debug, false);
   }
   if (tw[0]) {
     cudaError_t e = st == PW_OK ? cudaEventRecord(tw[1], stream) : cudaSuccess;
@@ -775,9 +821,11 @@ static pw_status graph_batch(pw_graph* g, int64_t count, const char* h, char* ho
   pw_status st = batch_buffers(g, (size_t)count, total_K, ba, &B);  // allocations stay outside the capture
   if (st != PW_OK) return st;
   const bool table_ok = table_bytes(g) <= kMaxTableBytes;
-  if (table_ok) table_grid<false>(g, table_bytes(g));
-  walk_grid<false, false>(g);
-  walk_grid<false, true>(g);
+  if (table_ok) {  // occupancy queries stay outside the capture
+    const WalkFn tf = table_fn(false, g->layout == 2, table_threads(g));
+    grid_of(g, tf, table_threads(g), table_bytes(g));
+  }
+  for (int pilot = 0; pilot < 2; ++pilot) grid_of(g, walk_fn(false, pilot != 0, g->layout == 2, g->visit_minb), kWalkThreads, 0);
   std::vector<unsigned char> key;
   key_put(key, count);
   key_put(key, total_K);
@@ -785,6 +833,8 @@ static pw_status graph_batch(pw_graph* g, int64_t count, const char* h, char* ho
   key_put(key, params ? params->walk_mode : 0);
   key_put(key, g->table_probe_cost);
   key_put(key, g->table_visit_gain);
+  key_put(key, g->visit_minb);
+  key_put(key, g->table_threads);
   key_put(key, B);
   key_put(key, ws.queries.ptr);
   key_put(key, ws.results.ptr);
@@ -1181,7 +1231,7 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
     out->queries = P.queries;
     PW_CUDA_TRY(cudaEventSynchronize(g->ws.last_use));
     out->walk_mode = last_walk_mode(g);
-    out->reserved = 0;
+    out->layout = g->layout;
     out->series_ms = P.series_ms;
     out->series_steps = P.series_steps;
   }
@@ -1193,11 +1243,13 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
   return PW_OK;
 }
 
-// Walk-kernel autotuner: time the sample in each walk kernel and fit the
-// graph's cost model (per-visit: visits * visit_ns; table: probes * probe_ns +
-// visits * table_visit_ns).  The two table runs differ only in L, which moves
-// the visits but not the probes (K depends on eps alone), so the pair of
-// timings separates the table build from the table walks.
+// Walk-kernel autotuner: time the sample in each walk kernel and its variants,
+// keep the fastest variant of each, and fit the graph's cost model (per-visit:
+// visits * visit_ns; table: probes * probe_ns + visits * table_visit_ns).  The
+// runs use a FIXED budget (B = 4 probes per block, the caller's G, R = 1024 or
+// 256 replicas), so the two table runs have the same probes and visits in the
+// ratio 4: their timings separate the table build from the table walks.  (A
+// PILOT budget would not do: its R follows the pilot, which depends on L.)
 pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
                       const int32_t* L, const uint64_t* seeds, const pw_params* params, pw_tune_result* out) {
   if (!g || !out) return set_error(PW_ERR_ARG, "NULL argument");
@@ -1206,29 +1258,35 @@ pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_
   std::lock_guard<std::mutex> guard(g->lock);
   PW_CUDA_TRY(cudaSetDevice(g->device));
   memset(out, 0, sizeof *out);
+  BudgetArgs ba;
+  pw_status st = resolve_budget(params, g, &ba, nullptr);
+  if (st != PW_OK) return st;
   pw_params p;
   if (params)
     p = *params;
   else
     memset(&p, 0, sizeof p);
+  p.budget_mode = PW_BUDGET_FIXED;
+  p.B = 4;
+  p.G = ba.G;
+  const uint64_t R_hi = 1024, R_lo = 256;
   const size_t nq = (size_t)count;
   std::vector<double> beta(nq);
   std::vector<int32_t> status(nq);
-  std::vector<int32_t> L4(nq);
-  for (size_t i = 0; i < nq; ++i) L4[i] = L[i] >= 4 ? L[i] / 4 : 4 * L[i];
-  // one warm-up and one timed run of the sample in walk kernel `mode`
   // probes and visits of each timed run, from its totals
   struct Run {
     DebugOut d;
     double n_probes = 0, n_visits = 0;
   };
-  auto timed = [&](int mode, const int32_t* Ls, Run* r) -> pw_status {
+  // one warm-up and one timed run of the sample in walk kernel `mode` with R replicas
+  auto timed = [&](int mode, uint64_t R, Run* r) -> pw_status {
     p.walk_mode = mode;
+    p.R = R;
     for (int rep = 0; rep < 2; ++rep) {
       r->d = DebugOut();
       r->d.time_walk = true;
-      const pw_status st = host_batch(g, count, s, t, eps, Ls, seeds, &p, beta.data(), status.data(), &r->d);
-      if (st != PW_OK) return st;
+      const pw_status st2 = host_batch(g, count, s, t, eps, L, seeds, &p, beta.data(), status.data(), &r->d);
+      if (st2 != PW_OK) return st2;
     }
     r->n_probes = (double)g->ws.host_totals->probes;
     r->n_visits = (double)g->ws.host_totals->visits;
@@ -1237,8 +1295,19 @@ pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_
     return PW_OK;
   };
   Run dv, dt, dq;
-  pw_status st = timed(1, L, &dv);
-  if (st != PW_OK) return st;
+  // per-visit kernel: registers left to the compiler or capped for 3 blocks/SM
+  int best_minb = 1;
+  for (int minb : {1, 3}) {
+    g->visit_minb = minb;
+    Run r;
+    if ((st = timed(1, R_hi, &r)) != PW_OK) return st;
+    if (minb == 1 || r.d.walk_ms < dv.d.walk_ms) {
+      dv = r;
+      best_minb = minb;
+    }
+  }
+  g->visit_minb = best_minb;
+  out->visit_occupancy = best_minb;
   out->sample_ms[0] = dv.d.walk_ms;
   out->visit_ns = dv.n_visits > 0 ? 1e6 * dv.d.walk_ms / dv.n_visits : 0.0;
   out->sample_mode = 1;
@@ -1248,8 +1317,20 @@ pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_
     return PW_OK;
   }
   out->table_available = 1;
-  if ((st = timed(2, L, &dt)) != PW_OK) return st;
-  if ((st = timed(2, L4.data(), &dq)) != PW_OK) return st;
+  // table kernel: block size
+  int best_threads = 256;
+  for (int threads : {256, 512, 1024}) {
+    g->table_threads = threads;
+    Run r;
+    if ((st = timed(2, R_hi, &r)) != PW_OK) return st;
+    if (threads == 256 || r.d.walk_ms < dt.d.walk_ms) {
+      dt = r;
+      best_threads = threads;
+    }
+  }
+  g->table_threads = best_threads;
+  out->table_threads = best_threads;
+  if ((st = timed(2, R_lo, &dq)) != PW_OK) return st;
   out->sample_ms[1] = dt.d.walk_ms;
   out->sample_ms[2] = dq.d.walk_ms;
   // solve  T = P c + V w  for the two table runs (times in ns)

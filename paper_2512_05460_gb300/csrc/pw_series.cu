@@ -13,7 +13,7 @@
 // row-major (a node's 32 pairs are one 256-byte row), so gathering x over a
 // node's neighbours reads whole lines.  Iteration i adds x_i to h and forms
 // x_{i+1} = P x_i with (P x)_v = (sum_{u in N(v)} x_u) * (1/d_v), neighbours
-// taken from the same 16-byte records the walks use.  Rows of at most 1024
+// read from col_idx (4 bytes per entry).  Rows of at most 1024
 // entries take one warp each and add in CSR order; longer rows (the hubs of
 // power-law graphs) are cut into 1024-entry segments whose partial sums are
 // added in segment order, so one hub does not hold up a whole step.
@@ -104,12 +104,12 @@ __global__ void series_inv_degree_kernel(const int4* __restrict__ node, float2* 
 // Sum of x_u (column = lane) over the neighbour entries [e0, e1) of one row,
 // added in CSR order.  A warp loads 32 neighbour ids with one coalesced load
 // and keeps 8 row loads in flight before adding them in order.
-__device__ __forceinline__ float2 series_row_sum(const float2* __restrict__ x, const int4* __restrict__ rec,
+__device__ __forceinline__ float2 series_row_sum(const float2* __restrict__ x, const int32_t* __restrict__ col,
                                                  int32_t e0, int32_t e1, uint32_t lane) {
   float2 acc = make_float2(0.f, 0.f);
   for (int32_t b = e0; b < e1; b += 32) {
     const int cnt = e1 - b < 32 ? e1 - b : 32;
-    const int u_l = (int)lane < cnt ? __ldg(&rec[b + (int)lane].x) : 0;
+    const int u_l = (int)lane < cnt ? __ldg(&col[b + (int)lane]) : 0;
     int j = 0;
     for (; j + 8 <= cnt; j += 8) {
       float2 v[8];
@@ -134,7 +134,7 @@ __device__ __forceinline__ float2 series_row_sum(const float2* __restrict__ x, c
 // h_v += x_v; y_v = (sum over neighbours of x_u) * (1/d_v).  Heavier rows
 // are left to the segment kernels below.
 __global__ void __launch_bounds__(256) series_light_kernel(const float2* __restrict__ x, float2* __restrict__ y,
-                                                           float2* __restrict__ h, const int4* __restrict__ rec,
+                                                           float2* __restrict__ h, const int32_t* __restrict__ col,
                                                            const int4* __restrict__ node,
                                                            const float2* __restrict__ inv, uint32_t n, int last) {
   const uint32_t lane = threadIdx.x & 31u;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256) series_light_kernel(const float2* __restr
     if (nv.z <= kSeriesSegEdges) {
       const size_t row = (size_t)v * kSeriesCols + lane;
       h[row] = df_add(h[row], x[row]);
-      if (!last) y[row] = df_mul(series_row_sum(x, rec, nv.y, nv.y + nv.z, lane), __ldg(inv + v));
+      if (!last) y[row] = df_mul(series_row_sum(x, col, nv.y, nv.y + nv.z, lane), __ldg(inv + v));
     }
     nv = nv_next;
   }
@@ -156,13 +156,13 @@ __global__ void __launch_bounds__(256) series_light_kernel(const float2* __restr
 // One warp per segment of a heavy row: the partial sum of its entries.
 __global__ void __launch_bounds__(256) series_segment_kernel(const float2* __restrict__ x,
                                                              float2* __restrict__ partial,
-                                                             const int4* __restrict__ rec,
+                                                             const int32_t* __restrict__ col,
                                                              const int4* __restrict__ segs, int32_t nseg) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < (uint32_t)nseg; i += warps) {
     const int4 sg = __ldg(segs + i);  // {row, e_begin, e_end, partial slot}
-    partial[(size_t)sg.w * kSeriesCols + lane] = series_row_sum(x, rec, sg.y, sg.z, lane);
+    partial[(size_t)sg.w * kSeriesCols + lane] = series_row_sum(x, col, sg.y, sg.z, lane);
   }
 }
 
@@ -304,11 +304,11 @@ extern "C" pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* 
     kernels += 2;
     for (int32_t i = 0; i <= Lc; ++i) {
       const int last = i == Lc;
-      series_light_kernel<<<grid, threads, 0, stream>>>(x, y, h, g->d_rec, g->d_node, inv, (uint32_t)n, last);
+      series_light_kernel<<<grid, threads, 0, stream>>>(x, y, h, g->d_col, g->d_node, inv, (uint32_t)n, last);
       ++kernels;
       if (nheavy > 0) {
         if (!last) {
-          series_segment_kernel<<<seg_grid, threads, 0, stream>>>(x, (float2*)partb.ptr, g->d_rec,
+          series_segment_kernel<<<seg_grid, threads, 0, stream>>>(x, (float2*)partb.ptr, g->d_col,
                                                                   (const int4*)segb.ptr, nseg);
           ++kernels;
         }

@@ -61,7 +61,8 @@ struct Completion {
 };
 
 struct ServerArgs {
-  const int4* rec;
+  const int4* rec;     // fused records (layout 1)
+  const int32_t* col;  // col_idx (layout 2)
   const int4* node;
   uint32_t n;
   uint32_t table_words;  // 0: graph too large for a shared-memory table
@@ -158,19 +159,33 @@ __device__ bool find_job(const ServerArgs& A, uint32_t& slot, uint32_t& stage, u
 // separate function.  Inlined into the job loop below, the same code ran about
 // 20x slower per walk step on a 4M-node grid (identical results); behind a call
 // boundary it runs at walk_kernel's speed.
-__device__ __noinline__ float server_walk_visit(const int4* __restrict__ rec, const int4* __restrict__ node,
-                                                uint32_t n, uint32_t walk_tag, uint32_t probe_tag, int32_t s,
-                                                int32_t t, int32_t L, uint64_t seed, uint32_t k, uint64_t pair) {
+template <class GR>
+__device__ __noinline__ float server_walk_visit(const GR gr, uint32_t n, uint32_t walk_tag, uint32_t probe_tag,
+                                                int32_t s, int32_t t, int32_t L, uint64_t seed, uint32_t k,
+                                                uint64_t pair) {
   const Probe pr = make_probe(n, seed, k, probe_tag);
   const ZOnTheFly zp{pr};
-  return walk_pair<false>(rec, node, nullptr, walk_tag, zp, s, t, L, seed, pair);
+  return walk_pair<false>(gr, nullptr, walk_tag, zp, s, t, L, seed, pair);
 }
 
 // TABLE: the graph's probe table fits in shared memory, so main-stage jobs may
 // use it (4 blocks/SM); without it only per-visit jobs exist and the kernel
 // keeps the registers that path needs (no occupancy cap).
-template <bool TABLE>
+// The graph access of the server: fused records, or col_idx plus node records.
+template <class GR>
+__device__ __forceinline__ GR server_graph(const ServerArgs& A);
+template <>
+__device__ __forceinline__ FusedRecords server_graph<FusedRecords>(const ServerArgs& A) {
+  return FusedRecords{A.rec, A.node};
+}
+template <>
+__device__ __forceinline__ SplitRecords server_graph<SplitRecords>(const ServerArgs& A) {
+  return SplitRecords{A.col, A.node};
+}
+
+template <bool TABLE, class GR>
 __global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(ServerArgs A) {
+  const GR gr = server_graph<GR>(A);
   extern __shared__ uint32_t smem[];
   uint32_t* tab = smem;
   double* means = (double*)(smem + A.table_words);  // table_words is a multiple of 4
@@ -219,9 +234,9 @@ __global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(S
         float U;
         if (TABLE && table) {
           const ZTable zp = table_reader(tab, A.n);
-          U = walk_pair_table<false>(A.rec, A.node, nullptr, walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
+          U = walk_pair_table<false>(gr, nullptr, walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
         } else {
-          U = server_walk_visit(A.rec, A.node, A.n, walk_tag, probe_tag, P.s, P.t, P.L, P.seed, k, pair);
+          U = server_walk_visit<GR>(gr, A.n, walk_tag, probe_tag, P.s, P.t, P.L, P.seed, k, pair);
         }
         sum_add(sum, U);
       }
@@ -311,6 +326,12 @@ __global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(S
     }
     __syncthreads();
   }
+}
+
+using ServerFn = void (*)(ServerArgs);
+static ServerFn server_fn(bool table, int layout) {
+  if (layout == 2) return table ? server_kernel<true, SplitRecords> : server_kernel<false, SplitRecords>;
+  return table ? server_kernel<true, FusedRecords> : server_kernel<false, FusedRecords>;
 }
 
 struct Request {
@@ -412,6 +433,7 @@ static void pool_free(pw_server* sv, size_t off, size_t bytes) {
 static ServerArgs server_args(pw_server* sv) {
   ServerArgs a;
   a.rec = sv->g->d_rec;
+  a.col = sv->g->d_col;
   a.node = sv->g->d_node;
   a.n = (uint32_t)sv->g->n;
   a.table_words = (uint32_t)((sv->smem - kServerMeansBytes) / sizeof(uint32_t));
@@ -541,10 +563,8 @@ static void worker_loop(pw_server* sv) {
         cudaStreamWaitEvent(sv->kstream, ev, 0);
         cudaEventDestroy(ev);
         cudaMemsetAsync(sv->d_ctl + 4, 0, sizeof(unsigned long long), sv->kstream);  // exit flag
-        if (args.table_words > 0)
-          server_kernel<true><<<sv->grid, kServerThreads, sv->smem, sv->kstream>>>(args);
-        else
-          server_kernel<false><<<sv->grid, kServerThreads, sv->smem, sv->kstream>>>(args);
+        const ServerFn fn = server_fn(args.table_words > 0, sv->g->layout);
+        fn<<<sv->grid, kServerThreads, sv->smem, sv->kstream>>>(args);
         count_launch();
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -631,15 +651,12 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
   const size_t tbytes = (sizeof(uint32_t) * (size_t)table_words((uint32_t)g->n) + 15) & ~(size_t)15;
   sv->smem = ubytes + ((tbytes + ubytes <= 200 * 1024) ? tbytes : 0);
   const bool with_table = sv->smem > ubytes;
-  if ((e = with_table ? cudaFuncSetAttribute(server_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sv->smem)
-                      : cudaFuncSetAttribute(server_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sv->smem)) != cudaSuccess)
+  const ServerFn fn = server_fn(with_table, g->layout);
+  if ((e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv->smem)) !=
+      cudaSuccess)
     return fail(cuda_error(e, "server smem attribute"));
   int nb = 0;
-  if ((e = with_table ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, server_kernel<true>, kServerThreads, sv->smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, server_kernel<false>, kServerThreads,
-                                                                      sv->smem)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kServerThreads, sv->smem)) != cudaSuccess)
     return fail(cuda_error(e, "server occupancy"));
   sv->grid = g->sm_count * (nb > 0 ? nb : 1);
   cudaDeviceSynchronize();

@@ -8,6 +8,34 @@
 
 namespace pw {
 
+// The graph as a walk reads it.  A node record is {v, row_start(v), deg(v),
+// bits of the FP32 reciprocal 1/deg(v)}; a step from record `cur` with random
+// word w moves to neighbour floor(w deg / 2^32) of the row (Algorithm 1's
+// uniform neighbour) and yields that neighbour's record.
+//   FusedRecords: rec[e] is the record of col[e]; one 16-byte gather per step.
+//     For graphs whose 16 B per entry sit comfortably in L2.
+//   SplitRecords: a 4-byte col[e] gather, then the neighbour's record from the
+//     n-entry node array; two dependent gathers into arrays 4x and nnz/n times
+//     smaller.  For graphs whose fused records would spill out of L2.
+struct FusedRecords {
+  const int4* __restrict__ rec;
+  const int4* __restrict__ node;
+  __device__ __forceinline__ int4 start(int32_t v) const { return __ldg(node + v); }
+  __device__ __forceinline__ int4 next(const int4& cur, uint32_t w) const {
+    return __ldg(rec + ((uint32_t)cur.y + __umulhi(w, (uint32_t)cur.z)));
+  }
+};
+
+struct SplitRecords {
+  const int32_t* __restrict__ col;
+  const int4* __restrict__ node;
+  __device__ __forceinline__ int4 start(int32_t v) const { return __ldg(node + v); }
+  __device__ __forceinline__ int4 next(const int4& cur, uint32_t w) const {
+    const int32_t u = __ldg(col + ((uint32_t)cur.y + __umulhi(w, (uint32_t)cur.z)));
+    return __ldg(node + u);
+  }
+};
+
 // Probe entries evaluated on the fly (Section 3.3 generator): one cycle-walk
 // queue for the two walks so a lane pays iter(s) + iter(t) Feistel passes.
 struct ZOnTheFly {
@@ -41,11 +69,10 @@ struct ZTable {
 // order (Eq. hatphi-def), U_p = a - b.  The load of X_{i+1} is issued before
 // the probe entry of X_i is evaluated so the gather latency overlaps the
 // integer work.
-template <bool DEBUG, class ZP>
-__device__ __forceinline__ float walk_pair(const int4* __restrict__ rec, const int4* __restrict__ node,
-                                           uint32_t* visits, uint32_t walk_tag, const ZP& zp, int32_t s,
+template <bool DEBUG, class GR, class ZP>
+__device__ __forceinline__ float walk_pair(const GR& gr, uint32_t* visits, uint32_t walk_tag, const ZP& zp, int32_t s,
                                            int32_t t, int32_t L, uint64_t seed, uint64_t pair) {
-  int4 xs = __ldg(node + s), xt = __ldg(node + t);
+  int4 xs = gr.start(s), xt = gr.start(t);
   int zs, zt;
   zp.pair((uint32_t)xs.x, (uint32_t)xt.x, zs, zt);
   float a = signed_term(zs, (uint32_t)xs.w);
@@ -61,8 +88,8 @@ __device__ __forceinline__ float walk_pair(const int4* __restrict__ rec, const i
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   Philox4 rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), 0u, walk_tag, k0, k1);
   Philox4 rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), 0u, walk_tag, k0, k1);
-  int4 ns = __ldg(rec + ((uint32_t)xs.y + __umulhi(rs.y, (uint32_t)xs.z)));
-  int4 nt = __ldg(rec + ((uint32_t)xt.y + __umulhi(rt.y, (uint32_t)xt.z)));
+  int4 ns = gr.next(xs, rs.y);
+  int4 nt = gr.next(xt, rt.y);
   for (uint32_t blk = 0;; ++blk) {
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
@@ -81,8 +108,8 @@ __device__ __forceinline__ float walk_pair(const int4* __restrict__ rec, const i
           wsw = (w == 0) ? rs.y : (w == 1) ? rs.z : rs.w;
           wtw = (w == 0) ? rt.y : (w == 1) ? rt.z : rt.w;
         }
-        ns2 = __ldg(rec + ((uint32_t)ns.y + __umulhi(wsw, (uint32_t)ns.z)));
-        nt2 = __ldg(rec + ((uint32_t)nt.y + __umulhi(wtw, (uint32_t)nt.z)));
+        ns2 = gr.next(ns, wsw);
+        nt2 = gr.next(nt, wtw);
       }
       zp.pair((uint32_t)ns.x, (uint32_t)nt.x, zs, zt);
       a = __fadd_rn(a, signed_term(zs, (uint32_t)ns.w));
@@ -107,11 +134,10 @@ __host__ __device__ __forceinline__ uint32_t table_words(uint32_t n) { return (n
 // issued, and the term of X_{i-1} (whose table word was read one step
 // earlier) is added.  The additions keep step order, so the result equals
 // walk_pair's bit for bit.
-template <bool DEBUG>
-__device__ __forceinline__ float walk_pair_table(const int4* __restrict__ rec, const int4* __restrict__ node,
-                                                 uint32_t* visits, uint32_t walk_tag, const ZTable& zt, int32_t s,
-                                                 int32_t t, int32_t L, uint64_t seed, uint64_t pair) {
-  const int4 xs = __ldg(node + s), xt = __ldg(node + t);
+template <bool DEBUG, class GR>
+__device__ __forceinline__ float walk_pair_table(const GR& gr, uint32_t* visits, uint32_t walk_tag, const ZTable& zt,
+                                                 int32_t s, int32_t t, int32_t L, uint64_t seed, uint64_t pair) {
+  const int4 xs = gr.start(s), xt = gr.start(t);
   float a = signed_term(zt.one((uint32_t)xs.x), (uint32_t)xs.w);
   float b = signed_term(zt.one((uint32_t)xt.x), (uint32_t)xt.w);
   if (DEBUG) {
@@ -123,8 +149,8 @@ __device__ __forceinline__ float walk_pair_table(const int4* __restrict__ rec, c
   const PhiloxKeys keys = philox_keys(seed);
   Philox4 rs = philox4x32_10((uint32_t)ws, (uint32_t)(ws >> 32), 0u, walk_tag, keys);
   Philox4 rt = philox4x32_10((uint32_t)wt, (uint32_t)(wt >> 32), 0u, walk_tag, keys);
-  int4 ns = __ldg(rec + ((uint32_t)xs.y + __umulhi(rs.y, (uint32_t)xs.z)));
-  int4 nt = __ldg(rec + ((uint32_t)xt.y + __umulhi(rt.y, (uint32_t)xt.z)));
+  int4 ns = gr.next(xs, rs.y);
+  int4 nt = gr.next(xt, rt.y);
   // pending term: table word, node and reciprocal of the previous step's nodes
   uint32_t ps_word = 0, pt_word = 0, ps_v = 0xFFFFFFFFu, pt_v = 0xFFFFFFFFu, ps_inv = 0, pt_inv = 0;
   bool pending = false;
@@ -146,8 +172,8 @@ __device__ __forceinline__ float walk_pair_table(const int4* __restrict__ rec, c
           wsw = (w == 0) ? rs.y : (w == 1) ? rs.z : rs.w;
           wtw = (w == 0) ? rt.y : (w == 1) ? rt.z : rt.w;
         }
-        ns2 = __ldg(rec + ((uint32_t)ns.y + __umulhi(wsw, (uint32_t)ns.z)));
-        nt2 = __ldg(rec + ((uint32_t)nt.y + __umulhi(wtw, (uint32_t)nt.z)));
+        ns2 = gr.next(ns, wsw);
+        nt2 = gr.next(nt, wtw);
       }
       const uint32_t cs_word = zt.tab[(uint32_t)ns.x >> 5], ct_word = zt.tab[(uint32_t)nt.x >> 5];
       if (pending) {

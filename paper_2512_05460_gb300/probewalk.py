@@ -23,6 +23,8 @@ PW_ERR_ARG, PW_ERR_GRAPH, PW_ERR_NOMEM, PW_ERR_CUDA = -1, -2, -3, -4
 PW_ERR_TIMEOUT, PW_ERR_CANCELLED, PW_ERR_FULL = -5, -6, -7
 PW_BUDGET_PILOT, PW_BUDGET_THEORY, PW_BUDGET_SCALED, PW_BUDGET_FIXED = 0, 1, 2, 3
 TAG_WALK, TAG_WALK_PILOT, TAG_PROBE, TAG_PROBE_PILOT = 1, 2, 3, 4
+# pw_graph_load flags: skip the connectivity check; force the fused or the split walk layout
+LOAD_NO_CONNECTIVITY, LOAD_FUSED, LOAD_SPLIT = 1, 2, 4
 
 _STATUS_NAMES = {0: "PW_OK", 1: "PW_PENDING", -1: "PW_ERR_ARG", -2: "PW_ERR_GRAPH", -3: "PW_ERR_NOMEM",
                  -4: "PW_ERR_CUDA", -5: "PW_ERR_TIMEOUT", -6: "PW_ERR_CANCELLED", -7: "PW_ERR_FULL"}
@@ -70,7 +72,7 @@ class pw_profile_stats(ctypes.Structure):
         ("pilot_transitions", ctypes.c_uint64),
         ("queries", ctypes.c_uint64),
         ("walk_mode", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("layout", ctypes.c_int32),
         ("series_ms", ctypes.c_double),
         ("series_steps", ctypes.c_uint64),
     ]
@@ -84,6 +86,8 @@ class pw_tune_result(ctypes.Structure):
         ("sample_ms", ctypes.c_double * 3),
         ("table_available", ctypes.c_int32),
         ("sample_mode", ctypes.c_int32),
+        ("visit_occupancy", ctypes.c_int32),
+        ("table_threads", ctypes.c_int32),
     ]
 
 
@@ -458,7 +462,8 @@ def pw_autotune(g: int, s, t, eps, L, seeds=None, params=None) -> dict:
                              None if sd is None else _p(sd, _u64), _params(params), ctypes.byref(out)))
     return {"visit_ns": out.visit_ns, "table_visit_ns": out.table_visit_ns, "table_probe_ns": out.table_probe_ns,
             "sample_ms": list(out.sample_ms), "table_available": out.table_available,
-            "sample_mode": out.sample_mode}
+            "sample_mode": out.sample_mode, "visit_occupancy": out.visit_occupancy,
+            "table_threads": out.table_threads}
 
 
 def pw_profile(g: int, enable: bool = True, reset: bool = False) -> dict:

@@ -43,9 +43,15 @@ def test_autotune_fits_and_auto_mode_follows_it(pw):
     assert r["table_probe_ns"] >= 0 and r["table_visit_ns"] >= 0
     assert r["table_probe_ns"] + r["table_visit_ns"] > 0
     assert r["sample_mode"] in (1, 2)
+    assert r["visit_occupancy"] in (1, 3) and r["table_threads"] in (256, 512, 1024)
+    # the auto mode gives each query the kernel the fitted model picks for it
+    _, _, KR, _ = pw.pw_debug_batch_probe_q(g.handle, s, t, eps, L, seeds, [], [])
+    gain = r["visit_ns"] - r["table_visit_ns"]
+    table = [r["table_probe_ns"] < 2.0 * float(R) * (L + 1) * gain for K, R in KR if K > 0]
+    want_mode = (1 if not all(table) else 0) | (2 if any(table) else 0)
     pw.pw_profile(g.handle, enable=True, reset=True)
     b0, m0 = _batch(pw, g, s, t, eps, L, seeds, 0)
-    assert m0 == r["sample_mode"]
+    assert m0 == want_mode
     b1, m1 = _batch(pw, g, s, t, eps, L, seeds, 1)
     b2, m2 = _batch(pw, g, s, t, eps, L, seeds, 2)
     assert (m1, m2) == (1, 2)

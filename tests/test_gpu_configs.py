@@ -1,8 +1,8 @@
 """Parity at the larger workload sizes, in the launch configuration the
-library picks for them: R-MAT 2^20 (646K nodes, 31M entries, records beyond
-L2, probe-table kernel) and the 2000x2000 grid with 5% of edges deleted
-(4M nodes; table too large for shared memory, per-visit kernel).  The oracle
-recomputes sampled probes one by one."""
+library picks for them: R-MAT 2^20 (646K nodes, 31M entries; split layout,
+walk kernel per query) and the 2000x2000 grid with 5% of edges deleted (4M
+nodes; split layout; table too large for shared memory, per-visit kernel).
+The oracle recomputes sampled probes one by one."""
 
 import numpy as np
 import pytest
@@ -24,8 +24,10 @@ def pw():
     return probewalk
 
 
-def _sampled_parity(pw, host, s, t, eps, L, seeds, n_sel=6):
+def _sampled_parity(pw, host, s, t, eps, L, seeds, n_sel=6, layout=None):
     with pw.Graph(host.row_ptr, host.col_idx) as g:
+        if layout is not None:
+            assert pw.pw_profile(g.handle, enable=False)["layout"] == layout
         rng = np.random.default_rng(5)
         sel_q = rng.integers(0, s.size, size=n_sel)
         sel_k = np.zeros(n_sel, np.int64)  # probe 0 exists for every query; resampled below
@@ -45,7 +47,7 @@ def test_rmat20_sampled_probes(pw, oracle_lib):
     host = rmat(20, 16, (0.57, 0.19, 0.19, 0.05), 2)
     s, t = uniform_pairs(host.n, 4, 102)
     eps = eps_uniform(4, 0.05, 0.2, 102)
-    _sampled_parity(pw, host, s, t, eps, np.full(4, 500, np.int32), query_seeds(4, 1002))
+    _sampled_parity(pw, host, s, t, eps, np.full(4, 500, np.int32), query_seeds(4, 1002), layout=2)
 
 
 def test_grid_sampled_probes(pw, oracle_lib):
@@ -53,7 +55,7 @@ def test_grid_sampled_probes(pw, oracle_lib):
     assert host.is_bipartite()
     s, t = uniform_pairs(host.n, 4, 103)
     eps = eps_choice(4, [0.05, 0.1, 0.2], 103)
-    _sampled_parity(pw, host, s, t, eps, np.full(4, 2000, np.int32), query_seeds(4, 1003))
+    _sampled_parity(pw, host, s, t, eps, np.full(4, 2000, np.int32), query_seeds(4, 1003), layout=2)
 
 
 def test_rmat24_sampled_probes(pw, oracle_lib):
@@ -64,4 +66,4 @@ def test_rmat24_sampled_probes(pw, oracle_lib):
     host = rmat_native(24, 16, (0.57, 0.19, 0.19, 0.05), 4)
     s, t = uniform_pairs(host.n, 3, 104)
     eps = eps_uniform(3, 0.05, 0.2, 104)
-    _sampled_parity(pw, host, s, t, eps, np.full(3, 1000, np.int32), query_seeds(3, 1004), n_sel=4)
+    _sampled_parity(pw, host, s, t, eps, np.full(3, 1000, np.int32), query_seeds(3, 1004), n_sel=4, layout=2)

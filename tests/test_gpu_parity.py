@@ -141,6 +141,38 @@ def test_mixed_walk_kernels_in_one_batch(pw, oracle_lib, tiny):
         np.testing.assert_array_equal(forced, want)
 
 
+@pytest.mark.parametrize("graph_fn", [lambda: er_cycle(200, 8 / 199, 0), lambda: barabasi_albert(3000, 3, 5)])
+def test_layouts_give_the_same_walks(pw, oracle_lib, graph_fn):
+    """Fused records (one 16-byte gather per step) and col_idx plus node
+    records (two gathers) give the same trajectories and the same estimates,
+    in both walk kernels and the server."""
+    host = graph_fn()
+    s, t = uniform_pairs(host.n, 8, 440)
+    seeds = query_seeds(8, 441)
+    want, _, _ = oracle.query_many(host, s, t, 0.25, 20, seeds)
+    for flags, layout in ((pw.LOAD_FUSED, 1), (pw.LOAD_SPLIT, 2)):
+        with pw.Graph(host.row_ptr, host.col_idx, flags=flags) as g:
+            assert pw.pw_profile(g.handle, enable=False)["layout"] == layout
+            for w in range(5):
+                np.testing.assert_array_equal(pw.pw_debug_walk(g.handle, int(s[w]), 30, 99, w),
+                                              oracle.walk(host, int(s[w]), 30, 99, w))
+            for mode in (1, 2):
+                b, st = pw.pw_query_batch(g.handle, s, t, 0.25, 20, seeds, pw.make_params(walk_mode=mode))
+                assert np.all(st == 0)
+                np.testing.assert_array_equal(b, want)
+            srv = pw.pw_server_create(g.handle, None, 1 << 24)
+            try:
+                tk = [pw.pw_server_submit(srv, int(s[i]), int(t[i]), 0.25, 20, int(seeds[i])) for i in range(8)]
+                pw.pw_server_drain(srv, 60000)
+                got = [pw.pw_server_poll(srv, x)[1] for x in tk]
+            finally:
+                pw.pw_server_destroy(srv)
+            np.testing.assert_array_equal(got, want)
+            ok = pw.pw_series_batch(g.handle, s, t, np.full(8, 20, np.int32))
+            np.testing.assert_allclose(ok, exact.series_beta_many(host.row_ptr, host.col_idx, host.n, s, t, 20),
+                                       rtol=1e-9, atol=0)
+
+
 def test_repeated_calls_replay_a_cuda_graph(pw, oracle_lib, tiny):
     """A host-array call runs eagerly the first time its shape is seen, is
     captured as a CUDA graph the second time and replayed afterwards: every
