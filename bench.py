@@ -241,6 +241,9 @@ def run_server(pw, g, s, t, eps, L, seeds, params, want):
     srv = pw.pw_server_create(g.handle, params, 4 << 30)
     out = {}
     try:
+        k = min(nq, 32)
+        out["tune"] = pw.pw_server_tune(srv, s[:k], t[:k], eps[:k], L[:k], seeds[:k])
+        out["tune"]["sample"] = f"first {k} queries, burst timed after a warm-up burst, per policy"
         t0 = time.perf_counter()
         tickets = [pw.pw_server_submit(srv, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i]))
                    for i in range(nq)]
@@ -276,6 +279,152 @@ def run_server(pw, g, s, t, eps, L, seeds, params, want):
     finally:
         pw.pw_server_destroy(srv)
     return out
+
+
+def run_serving(args, wl, world, rank, local):
+    """Serving on the workload's graph: a burst of --burst queries measures the
+    server's capacity, then Poisson streams of --queries queries arrive at
+    --loads x that capacity; latency is submit to completion (p50, p99,
+    p99.9), throughput is completions / wall time, clocks are sampled while the
+    streams run.  Query pairs, eps and seeds follow the workload's recipe."""
+    import torch
+
+    from paper_2512_05460_gb300 import build as pwbuild
+    from pw_inputs import poisson_arrivals, query_seeds, uniform_pairs, workload_graph
+
+    pwbuild.build()
+    from paper_2512_05460_gb300 import probewalk as pw
+
+    torch.cuda.set_device(local)
+    n = args.queries or 1000
+    host = workload_graph(wl["graph"])
+    s, t = uniform_pairs(host.n, n, wl["pair_seed"] + 7919 * rank)
+    seeds = query_seeds(n, wl["seed_seed"] + 7919 * rank)
+    eps = workload_eps(wl, n, rank)
+    L = wl["L"]
+    g = pw.Graph(host.row_ptr, host.col_idx, device=local)
+    if not args.no_autotune:
+        k = min(n, 8)
+        pw.pw_autotune(g.handle, s[:k], t[:k], eps[:k], np.full(k, L, np.int32), seeds[:k])
+    srv = pw.pw_server_create(g.handle, None, 8 << 30)
+    out = {}
+    try:
+        k = min(n, 32)
+        out["tune"] = pw.pw_server_tune(srv, s[:k], t[:k], eps[:k], np.full(k, L, np.int32), seeds[:k])
+        nb = min(n, args.burst)
+        t0 = time.perf_counter()
+        for i in range(nb):
+            pw.pw_server_submit(srv, int(s[i]), int(t[i]), float(eps[i]), L, int(seeds[i]))
+        pw.pw_server_drain(srv, 3600 * 1000)
+        burst_s = time.perf_counter() - t0
+        _, _, st, lat = pw.pw_server_collect(srv, 4 * n)
+        assert np.all(st == 0)
+        cap = nb / burst_s
+        out["burst"] = {"queries": nb, "queries_per_s": cap, "p50_ms": float(np.percentile(lat, 50)),
+                        "p99_ms": float(np.percentile(lat, 99))}
+        loads = []
+        for frac in (float(x) for x in args.loads.split(",")):
+            rate = frac * cap
+            arr = poisson_arrivals(n, rate, 4242 + int(100 * frac))
+            sampler = ClockSampler(local)
+            sampler.start()
+            t0 = time.perf_counter()
+            for i in range(n):
+                d = arr[i] - (time.perf_counter() - t0)
+                if d > 0:
+                    time.sleep(d)
+                pw.pw_server_submit(srv, int(s[i]), int(t[i]), float(eps[i]), L, int(seeds[i]))
+            pw.pw_server_drain(srv, 3600 * 1000)
+            wall = time.perf_counter() - t0
+            clocks = sampler.stop()
+            _, _, st, lat = pw.pw_server_collect(srv, 4 * n)
+            assert np.all(st == 0)
+            loads.append({"offered_frac_of_capacity": frac, "offered_qps": rate, "achieved_qps": n / wall,
+                          "queries": n, "p50_ms": float(np.percentile(lat, 50)),
+                          "p99_ms": float(np.percentile(lat, 99)), "p999_ms": float(np.percentile(lat, 99.9)),
+                          "wall_s": wall, "clocks": clocks})
+        out["poisson"] = loads
+    finally:
+        pw.pw_server_destroy(srv)
+    line = {"metric": "serving: queries/s and p50/p99 latency of Poisson streams (continuous batching)",
+            "unit": "queries/s", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}; {n} uniform pairs per stream; L={L}; "
+                                   f"eps={wl['eps']}; PILOT budget c_B=0.5; 8 GiB accumulator pool"},
+            "server": out}
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
+def run_scale_batch(args, wl, world, rank, local):
+    """One batch of --queries queries (default 10,000) through
+    pw_query_batch_device: an untimed batch of the same size first (it sizes
+    the scratch and warms the kernels), then --steps timed batches with CUDA
+    events on the launch stream; reports queries/s, walk steps/s, the walk
+    kernels' share and the scratch the batch needed (Q_R and per-probe
+    accumulators: nothing per replica)."""
+    import torch
+
+    from paper_2512_05460_gb300 import build as pwbuild
+    from pw_inputs import query_seeds, uniform_pairs, workload_graph
+
+    pwbuild.build()
+    from paper_2512_05460_gb300 import probewalk as pw
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.queries or 10000
+    host = workload_graph(wl["graph"])
+    s, t = uniform_pairs(host.n, n, wl["pair_seed"] + 7919 * rank)
+    seeds = query_seeds(n, wl["seed_seed"] + 7919 * rank)
+    eps = workload_eps(wl, n, rank)
+    L = np.full(n, wl["L"], np.int32)
+    g = pw.Graph(host.row_ptr, host.col_idx, device=local)
+    params = pw.make_params(c_B=args.c_B)
+    tune = None
+    if not args.no_autotune:
+        k = min(n, 8)
+        tune = pw.pw_autotune(g.handle, s[:k], t[:k], eps[:k], L[:k], seeds[:k], params)
+    d = [torch.from_numpy(a).to(dev) for a in (s, t, eps, L, seeds.view(np.int64))]
+    beta = torch.empty(n, dtype=torch.float64, device=dev)
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    mem0 = torch.cuda.mem_get_info(dev)[0]
+    pw.pw_query_batch_device(g.handle, n, *d, beta, status, params, stream=stream)
+    stream.synchronize()
+    scratch = mem0 - torch.cuda.mem_get_info(dev)[0]
+    assert int(status.abs().sum()) == 0
+    sampler = ClockSampler(local)
+    pw.pw_profile(g.handle, enable=True, reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler.start()
+    for a, b in ev:
+        a.record(stream)
+        pw.pw_query_batch_device(g.handle, n, *d, beta, status, params, stream=stream)
+        b.record(stream)
+    stream.synchronize()
+    clocks = sampler.stop()
+    prof = pw.pw_profile(g.handle, enable=False, reset=True)
+    assert int(status.abs().sum()) == 0 and bool(torch.isfinite(beta).all())
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    hbm_peak, peak_kind = load_peaks()
+    gathers = 1 if prof["layout"] == 1 else 2
+    walk_s = prof["walk_ms"] / 1000.0
+    line = {"metric": "queries/s of one large batch (persistent walk kernels, per-query kernel choice)",
+            "value": n * args.steps / (ms / 1000.0), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": ms / args.steps, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}; {n} uniform pairs in one batch; L={wl['L']}; "
+                                   f"eps={wl['eps']}; PILOT budget c_B={args.c_B or 0.5}",
+                       "inputs": "device-resident (pw_query_batch_device)"},
+            "walk_steps_per_s": (prof["transitions"] + prof["pilot_transitions"]) / (ms / 1000.0),
+            "walk_share": prof["walk_ms"] / ms,
+            "walk_kernels": {1: "per-visit", 2: "table", 3: "both (chosen per query)"}.get(prof["walk_mode"]),
+            "roofline": {"bound": "hbm", "achieved": prof["transitions"] * 32 * gathers / walk_s / 1e9,
+                         "peak": hbm_peak, "unit": "GB/s", "peak_kind": peak_kind,
+                         "frac": prof["transitions"] * 32 * gathers / walk_s / 1e9 / hbm_peak,
+                         "bytes_model": f"{32 * gathers} B per walk transition"},
+            "scratch_bytes": int(scratch), "autotune": tune, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    g.close()
 
 
 def run_stabilized(args, wl, world, rank, local):
@@ -650,8 +799,12 @@ def run_ours(args, wl, world, rank, local):
     if record_bytes < L2_BYTES // 2:
         l2_peak = pw.pw_debug_gather_peak(g.handle, 2048) * SECTOR_BYTES * gathers / 1e9
         roofline = {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
-                    "peak_kind": "measured in this run: dependent random 16-B gathers over the same record array "
-                                 "(pw_debug_gather_peak)"}
+                    "peak_kind": "measured in this run: dependent random gathers with the walk's access over the "
+                                 "same L2-resident arrays (pw_debug_gather_peak)",
+                    "hbm_copy_peak": hbm_peak, "frac_of_hbm_copy_peak": achieved / hbm_peak,
+                    "hbm_copy_peak_kind": peak_kind,
+                    "note": "the arrays are L2-resident, so DRAM is idle; the headline fraction is against the "
+                            "measured L2 gather ceiling, the copy-peak fraction is context"}
     else:
         # Context beside the copy peak: the ceiling of this access pattern
         # (dependent random 16-B gathers, uniform over the same records, which
@@ -746,6 +899,10 @@ def main():
     ap.add_argument("--eps-sweep", action="store_true", help="runtime and error over eps (Fig. 2 protocol)")
     ap.add_argument("--series", action="store_true", help="the GPU truncated series beta^(L) (Lemma 2.3)")
     ap.add_argument("--accuracy", action="store_true", help="fraction within eps of beta^(L), by R_max")
+    ap.add_argument("--serving", action="store_true", help="server capacity and Poisson-stream latency")
+    ap.add_argument("--scale-batch", action="store_true", help="one large batch (--queries, default 10000)")
+    ap.add_argument("--burst", type=int, default=1000, help="queries of the --serving capacity burst")
+    ap.add_argument("--loads", default="0.5,0.9", help="offered loads of --serving, as fractions of capacity")
     ap.add_argument("--r-max", default="4096,8192,16384", help="R_max values of --accuracy")
     ap.add_argument("--c-B-list", default="0.5", help="c_B values of --accuracy")
     args = ap.parse_args()
@@ -761,6 +918,10 @@ def main():
         run_series(args, wl, world, rank, local)
     elif args.accuracy:
         run_accuracy(args, wl, world, rank, local)
+    elif args.serving:
+        run_serving(args, wl, world, rank, local)
+    elif args.scale_batch:
+        run_scale_batch(args, wl, world, rank, local)
     elif args.eps_sweep:
         run_eps_sweep(args, wl, world, rank, local)
     else:

@@ -260,6 +260,25 @@ pw_status pw_server_poll(pw_server* srv, uint64_t ticket, double* beta_hat);
  * collected ticket is delivered: pw_server_poll then reports PW_ERR_ARG. */
 pw_status pw_server_collect(pw_server* srv, int64_t cap, uint64_t* tickets, double* beta_hat, int32_t* status,
                             double* latency_ms, int64_t* count);
+/* Server tuning (an implementation choice: every policy gives the same
+ * estimates).  After a query's pilot the server runs its probes either with a
+ * per-probe shared-memory table of z or evaluating z at each visit; the
+ * choice follows a cost model {table cost per probe, saving per visit}.
+ * pw_server_tune runs the sample (host arrays as in pw_query_batch; seeds may
+ * be NULL) through the server as a burst, once to warm up and once timed,
+ * under each policy: 0 the default model (n Feistel passes per table against
+ * 2.5 per visit), 1 the graph's model fitted by pw_autotune on the batch
+ * kernels (skipped when the graph is untuned), 2 every query per-visit, 3
+ * every query with the table (skipped when the table does not fit).  It keeps
+ * the fastest and reports each policy's queries/s (0 for a skipped one).
+ * Call it on an idle server: the sample's tickets are consumed by the tuner. */
+typedef struct pw_server_tune_result {
+  double queries_per_s[4];
+  int32_t policy;          /* the policy kept */
+  int32_t reserved;
+} pw_server_tune_result;
+pw_status pw_server_tune(pw_server* srv, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
+                         const int32_t* L, const uint64_t* seeds, pw_server_tune_result* out);
 /* Wait up to timeout_ms for every submitted ticket; PW_ERR_TIMEOUT otherwise. */
 pw_status pw_server_drain(pw_server* srv, int64_t timeout_ms);
 /* Cancels requests still waiting for admission (their tickets get
@@ -336,8 +355,9 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
  * give bit-identical results, so the choice only changes speed.
  *
  * Runs the caller's sample batch (host arrays as in pw_query_batch, seeds may
- * be NULL, each query's s, t, L) with a FIXED budget of B = 4 probes per
- * block, params' G, and R = 1024 replicas, each run after one untimed
+ * be NULL, each query's s, t, L) with a FIXED budget of B = 16 probes per
+ * block (8 queries give 4,736 probes at G = 37, enough to fill the GPU),
+ * params' G, and R = 1024 replicas, each run after one untimed
  * warm-up: the per-visit kernel in its two register variants (compiler's
  * choice, or capped for 3 blocks of 256 per SM), keeping the faster; the
  * per-probe shared-memory table with blocks of 256, 512 and 1024 threads,
@@ -349,13 +369,15 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
  *   table:      t = probes * table_probe_ns + visits * table_visit_ns
  * (visits = 2 K R (L+1) summed over the batch) and stores the costs in the
  * graph: from then on walk_mode 0 (auto) in pw_query* uses the table when
- * probes * table_probe_ns < visits * (visit_ns - table_visit_ns).  Servers
- * keep the default model (their kernels differ from the batch kernels timed
- * here).  Costs are whole-GPU nanoseconds, so the sample
- * should fill the GPU (a few thousand probes).  When the graph's table does not
- * fit in shared memory (one bit per node in at most 200 KB: n > 1,638,336) only
- * the per-visit run is made and
- * table_available = 0; the model then always picks per-visit.  params as in
+ * probes * table_probe_ns < visits * (visit_ns - table_visit_ns).  Last,
+ * the sample runs once more at the caller's own budget under three policies
+ * (that model per query, every query per-visit, every query on the table),
+ * and walk_mode 0 follows the fastest from then on (with the table
+ * unavailable, policy 0 and 1 coincide).  Servers keep their own policy (see
+ * pw_server_tune).  Costs are whole-GPU nanoseconds.  When the graph's table
+ * does not fit in shared memory (one bit per node in at most 200 KB:
+ * n > 1,638,336) only the per-visit runs are made and table_available = 0;
+ * the model then always picks per-visit.  params as in
  * pw_query (its walk_mode is ignored).  Errors as pw_query_batch; the
  * estimates of the runs are discarded. */
 typedef struct pw_tune_result {
@@ -367,6 +389,9 @@ typedef struct pw_tune_result {
   int32_t sample_mode;     /* walk kernel the fitted model picks for the sample: 1 per-visit, 2 table */
   int32_t visit_occupancy; /* per-visit kernel variant kept: 1 compiler-chosen registers, 3 capped for 3 blocks/SM */
   int32_t table_threads;   /* table-kernel block size kept: 256, 512 or 1024 (0 when unavailable) */
+  double policy_ms[3];     /* walk time of the sample at the caller's budget: per-query model, all per-visit, all table */
+  int32_t policy;          /* the policy walk_mode 0 now follows: 0 per-query model, 1 all per-visit, 2 all table */
+  int32_t reserved;
 } pw_tune_result;
 pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
                       const int32_t* L, const uint64_t* seeds, const pw_params* params, pw_tune_result* out);

@@ -117,6 +117,7 @@ struct pw_graph {
   // block size (0: by shared memory, else 256, 512 or 1024 threads).
   int visit_minb = 1;
   int table_threads = 0;
+  int walk_policy = 0;  // walk_mode 0 means: 0 the cost model per query, 1 all per-visit, 2 all table
   std::mutex lock;
   pw::GraphCache gcache;
   pw::Workspace ws;

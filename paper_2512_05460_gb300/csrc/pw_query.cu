@@ -619,8 +619,10 @@ static pw_status enqueue_walks(pw_graph* g, int64_t count, const pw_params* para
     PW_CUDA_TRY(cudaGetLastError());
   }
   const bool table_ok = table_bytes(g) <= kMaxTableBytes;
-  ModeArgs M{params ? params->walk_mode : 0, table_ok ? 1 : 0, g->table_probe_cost, g->table_visit_gain};
-  if (M.forced < 0 || M.forced > 2) return set_error(PW_ERR_ARG, "walk_mode must be 0, 1 or 2");
+  const int forced = params && params->walk_mode ? params->walk_mode : g->walk_policy;
+  ModeArgs M{forced, table_ok ? 1 : 0, g->table_probe_cost, g->table_visit_gain};
+  if (params && (params->walk_mode < 0 || params->walk_mode > 2))
+    return set_error(PW_ERR_ARG, "walk_mode must be 0, 1 or 2");
   scan_kernel<<<1, 1024, 0, stream>>>(B.plans, count, prefix, B.totals, M);
   count_launch();
   PW_CUDA_TRY(cudaGetLastError());
@@ -834,6 +836,7 @@ static pw_status graph_batch(pw_graph* g, int64_t count, const char* h, char* ho
   key_put(key, g->table_probe_cost);
   key_put(key, g->table_visit_gain);
   key_put(key, g->visit_minb);
+  key_put(key, g->walk_policy);
   key_put(key, g->table_threads);
   key_put(key, B);
   key_put(key, ws.queries.ptr);
@@ -1266,8 +1269,9 @@ pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_
     p = *params;
   else
     memset(&p, 0, sizeof p);
+  const pw_params caller = p;
   p.budget_mode = PW_BUDGET_FIXED;
-  p.B = 4;
+  p.B = 16;
   p.G = ba.G;
   const uint64_t R_hi = 1024, R_lo = 256;
   const size_t nq = (size_t)count;
@@ -1358,6 +1362,29 @@ pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_
   g->tuned = 1;
   const double Vs = dv.n_visits, Ps = dv.n_probes;
   out->sample_mode = Ps * g->table_probe_cost < Vs * g->table_visit_gain ? 2 : 1;
+  // policy check on the caller's own budget (PILOT: R from the pilot): the
+  // fitted per-query model against every query per-visit and every query on
+  // the table, each timed once more; the fastest is kept
+  p = caller;
+  double best_ms = 0.0;
+  int best_policy = 0;
+  for (int policy : {0, 1, 2}) {
+    g->walk_policy = policy;
+    DebugOut d;
+    for (int rep = 0; rep < 2; ++rep) {
+      d = DebugOut();
+      d.time_walk = true;
+      p.walk_mode = 0;
+      if ((st = host_batch(g, count, s, t, eps, L, seeds, &p, beta.data(), status.data(), &d)) != PW_OK) return st;
+    }
+    out->policy_ms[policy] = d.walk_ms;
+    if (policy == 0 || d.walk_ms < best_ms) {
+      best_ms = d.walk_ms;
+      best_policy = policy;
+    }
+  }
+  g->walk_policy = best_policy;
+  out->policy = best_policy;
   return PW_OK;
 }
 

@@ -78,7 +78,7 @@ struct ServerArgs {
   unsigned long long* last_claim;  // %globaltimer of the latest job claim by any block
   uint32_t* exit_flag;             // set once the whole grid has been idle for idle_ns
   unsigned long long idle_ns;
-  double table_probe_cost, table_visit_gain;  // walk-mode cost model (the default one, see pw_server_create)
+  const double* model;  // device: walk-mode cost model {table cost per probe, saving per visit}
   BudgetArgs A;
 };
 
@@ -287,7 +287,8 @@ __global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(S
           // table when building z^(k) is cheaper than evaluating it at every
           // visit, by the graph's walk-mode cost model
           const double visits = 2.0 * (double)M.R * (double)(P.L + 1);
-          __stcg(&S->use_table, (A.table_words > 0 && A.table_probe_cost < A.table_visit_gain * visits) ? 1u : 0u);
+          const double probe_cost = __ldcg(A.model), visit_gain = __ldcg(A.model + 1);
+          __stcg(&S->use_table, (A.table_words > 0 && probe_cost < visit_gain * visits) ? 1u : 0u);
           __threadfence();
           const unsigned long long pos = atomicAdd(A.dtail, 1ull);
           const uint32_t idx = (uint32_t)(pos % A.cap) + A.cap;
@@ -381,7 +382,8 @@ struct pw_server {
   cudaStream_t kstream = nullptr, cstream = nullptr;
   size_t smem = 0;
   int grid = 0;
-  double table_probe_cost = 0.0, table_visit_gain = 0.0;  // walk-mode cost model (default constants)
+  double table_probe_cost = 0.0, table_visit_gain = 0.0;  // walk-mode cost model (host copy of d_model)
+  double* d_model = nullptr;
   bool kernel_live = false;
   uint32_t active = 0;
   std::thread worker;
@@ -449,8 +451,7 @@ static ServerArgs server_args(pw_server* sv) {
   a.comp = sv->d_comp;
   a.stop = sv->d_stop;
   a.idle_ns = 5ull * 1000 * 1000;
-  a.table_probe_cost = sv->table_probe_cost;
-  a.table_visit_gain = sv->table_visit_gain;
+  a.model = sv->d_model;
   a.A = sv->ba;
   return a;
 }
@@ -604,9 +605,9 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
   sv->ba = ba;
   // The default walk-mode model (n Feistel passes per table against 2.5 per
   // visit), not the graph's autotuned costs: those are fitted on the batch
-  // kernels, and the server's per-visit path runs inside the table-capable
-  // server kernel at its 64-register cap, so it is slower than walk_kernel and
-  // the batch costs would under-use the table (R-MAT 2^20: 29 vs 37 queries/s).
+  // kernels, whose per-visit path is faster than the server's (the server's
+  // runs inside the table-capable kernel at its register cap).
+  // pw_server_tune picks the server's own policy by timing it.
   sv->table_probe_cost = (double)g->n;
   sv->table_visit_gain = 2.5;
   sv->S = 4096;
@@ -624,6 +625,7 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
       (e = cudaMalloc(&sv->d_ring_stage, sizeof(uint32_t) * ring)) != cudaSuccess ||
       (e = cudaMalloc(&sv->d_ring_seq, sizeof(unsigned long long) * ring)) != cudaSuccess ||
       (e = cudaMalloc(&sv->d_stop, sizeof(uint32_t))) != cudaSuccess ||
+      (e = cudaMalloc(&sv->d_model, 2 * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&sv->d_pool, accum_bytes)) != cudaSuccess ||
       (e = cudaMallocHost(&sv->h_slot_stage, sizeof(SlotDev) * sv->S)) != cudaSuccess ||
       (e = cudaMallocHost(&sv->h_ring_stage_buf, sizeof(uint32_t) * 2 * sv->cap)) != cudaSuccess ||
@@ -635,7 +637,9 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
       (e = cudaStreamCreateWithFlags(&sv->cstream, cudaStreamNonBlocking)) != cudaSuccess)
     return fail(cuda_error(e, "server allocation"));
   memset(sv->h_comp, 0, sizeof(Completion) * sv->S);
-  if ((e = cudaMemset(sv->d_slots, 0, sizeof(SlotDev) * sv->S)) != cudaSuccess ||
+  const double model[2] = {sv->table_probe_cost, sv->table_visit_gain};
+  if ((e = cudaMemcpy(sv->d_model, model, sizeof model, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(sv->d_slots, 0, sizeof(SlotDev) * sv->S)) != cudaSuccess ||
       (e = cudaMemset(sv->d_ctl, 0, sizeof(unsigned long long) * 8)) != cudaSuccess ||
       (e = cudaMemset(sv->d_ring_seq, 0xFF, sizeof(unsigned long long) * ring)) != cudaSuccess ||
       (e = cudaMemset(sv->d_stop, 0, sizeof(uint32_t))) != cudaSuccess)
@@ -732,6 +736,57 @@ pw_status pw_server_drain(pw_server* sv, int64_t timeout_ms) {
   return PW_OK;
 }
 
+pw_status pw_server_tune(pw_server* sv, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
+                         const int32_t* L, const uint64_t* seeds, pw_server_tune_result* out) {
+  if (!sv || !out || !s || !t || !eps || !L || count <= 0) return set_error(PW_ERR_ARG, "NULL argument or empty sample");
+  memset(out, 0, sizeof *out);
+  pw_graph* g = sv->g;
+  const bool table = sv->smem > kServerMeansBytes;
+  // candidate policies {table cost per probe, saving per visit}: the default
+  // model, the graph's batch-fitted model, every query per-visit, every query
+  // on the table (last two only where meaningful)
+  const double cand[4][2] = {{(double)g->n, 2.5}, {g->table_probe_cost, g->table_visit_gain}, {1.0, 0.0}, {0.0, 1.0}};
+  const bool valid[4] = {true, g->tuned != 0, true, table};
+  int best = 0;
+  std::vector<uint64_t> tk((size_t)count);
+  for (int c = 0; c < 4; ++c) {
+    if (!valid[c]) continue;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->table_probe_cost = cand[c][0];
+      sv->table_visit_gain = cand[c][1];
+    }
+    PW_CUDA_TRY(cudaSetDevice(g->device));
+    PW_CUDA_TRY(cudaMemcpy(sv->d_model, cand[c], 2 * sizeof(double), cudaMemcpyHostToDevice));
+    double secs = 0.0;
+    for (int rep = 0; rep < 2; ++rep) {  // a warm-up burst, then the timed one
+      const double t0 = now_ms();
+      for (int64_t i = 0; i < count; ++i) {
+        const pw_status st = pw_server_submit(sv, s[i], t[i], eps[i], L[i], seeds ? seeds + i : nullptr, &tk[(size_t)i]);
+        if (st != PW_OK) return st;
+      }
+      pw_status st = pw_server_drain(sv, 3600 * 1000);
+      if (st != PW_OK) return st;
+      secs = (now_ms() - t0) / 1000.0;
+      for (int64_t i = 0; i < count; ++i) {
+        double b;
+        st = pw_server_poll(sv, tk[(size_t)i], &b);
+        if (st != PW_OK) return set_error(st, "pw_server_tune: a sample query failed");
+      }
+    }
+    out->queries_per_s[c] = (double)count / secs;
+    if (out->queries_per_s[c] > out->queries_per_s[best]) best = c;
+  }
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->table_probe_cost = cand[best][0];
+    sv->table_visit_gain = cand[best][1];
+  }
+  PW_CUDA_TRY(cudaMemcpy(sv->d_model, cand[best], 2 * sizeof(double), cudaMemcpyHostToDevice));
+  out->policy = best;
+  return PW_OK;
+}
+
 pw_status pw_server_destroy(pw_server* sv) {
   if (!sv) return PW_OK;
   cudaSetDevice(sv->g->device);
@@ -760,6 +815,7 @@ pw_status pw_server_destroy(pw_server* sv) {
   cudaFree(sv->d_ring_stage);
   cudaFree(sv->d_ring_seq);
   cudaFree(sv->d_stop);
+  cudaFree(sv->d_model);
   cudaFree(sv->d_pool);
   if (sv->h_slot_stage) cudaFreeHost(sv->h_slot_stage);
   if (sv->h_ring_stage_buf) cudaFreeHost(sv->h_ring_stage_buf);

@@ -62,6 +62,10 @@ def make_params(**kw) -> pw_params:
     return p
 
 
+class pw_server_tune_result(ctypes.Structure):
+    _fields_ = [("queries_per_s", ctypes.c_double * 4), ("policy", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class pw_profile_stats(ctypes.Structure):
     _fields_ = [
         ("walk_ms", ctypes.c_double),
@@ -88,6 +92,9 @@ class pw_tune_result(ctypes.Structure):
         ("sample_mode", ctypes.c_int32),
         ("visit_occupancy", ctypes.c_int32),
         ("table_threads", ctypes.c_int32),
+        ("policy_ms", ctypes.c_double * 3),
+        ("policy", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -122,6 +129,7 @@ SIGNATURES = {
     "pw_server_poll": (_i32, [_vp, _u64, P(_dbl)]),
     "pw_server_collect": (_i32, [_vp, _i64, P(_u64), P(_dbl), P(_i32), P(_dbl), P(_i64)]),
     "pw_server_drain": (_i32, [_vp, _i64]),
+    "pw_server_tune": (_i32, [_vp, _i64, P(_i64), P(_i64), P(_dbl), P(_i32), P(_u64), P(pw_server_tune_result)]),
     "pw_server_destroy": (_i32, [_vp]),
     "pw_debug_philox": (_i32, [_vp, P(_u32), P(_u32), P(_u32)]),
     "pw_debug_probe": (_i32, [_vp, _u64, _u32, _u32, P(ctypes.c_int8), P(_i32)]),
@@ -363,6 +371,20 @@ def pw_server_drain(srv: int, timeout_ms: int = 60000) -> None:
     _check(lib().pw_server_drain(srv, timeout_ms))
 
 
+def pw_server_tune(srv: int, s, t, eps, L, seeds=None) -> dict:
+    """Time the sample through the server under each walk-kernel policy and keep the fastest."""
+    s = _arr(s, np.int64)
+    n = s.size
+    t = _arr(t, np.int64)
+    eps = _arr(np.broadcast_to(eps, (n,)), np.float64)
+    L = _arr(np.broadcast_to(L, (n,)), np.int32)
+    sd = None if seeds is None else _arr(seeds, np.uint64)
+    out = pw_server_tune_result()
+    _check(lib().pw_server_tune(srv, n, _p(s, _i64), _p(t, _i64), _p(eps, _dbl), _p(L, _i32),
+                                None if sd is None else _p(sd, _u64), ctypes.byref(out)))
+    return {"queries_per_s": list(out.queries_per_s), "policy": out.policy}
+
+
 def pw_server_destroy(srv: int) -> None:
     _check(lib().pw_server_destroy(srv))
 
@@ -463,7 +485,7 @@ def pw_autotune(g: int, s, t, eps, L, seeds=None, params=None) -> dict:
     return {"visit_ns": out.visit_ns, "table_visit_ns": out.table_visit_ns, "table_probe_ns": out.table_probe_ns,
             "sample_ms": list(out.sample_ms), "table_available": out.table_available,
             "sample_mode": out.sample_mode, "visit_occupancy": out.visit_occupancy,
-            "table_threads": out.table_threads}
+            "table_threads": out.table_threads, "policy_ms": list(out.policy_ms), "policy": out.policy}
 
 
 def pw_profile(g: int, enable: bool = True, reset: bool = False) -> dict:

@@ -49,6 +49,11 @@ def test_autotune_fits_and_auto_mode_follows_it(pw):
     gain = r["visit_ns"] - r["table_visit_ns"]
     table = [r["table_probe_ns"] < 2.0 * float(R) * (L + 1) * gain for K, R in KR if K > 0]
     want_mode = (1 if not all(table) else 0) | (2 if any(table) else 0)
+    # ... unless the timed policy check kept "all per-visit" or "all table"
+    assert r["policy"] in (0, 1, 2) and all(x > 0 for x in r["policy_ms"])
+    assert r["policy_ms"][r["policy"]] == min(r["policy_ms"])
+    if r["policy"] != 0:
+        want_mode = r["policy"]
     pw.pw_profile(g.handle, enable=True, reset=True)
     b0, m0 = _batch(pw, g, s, t, eps, L, seeds, 0)
     assert m0 == want_mode

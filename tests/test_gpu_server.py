@@ -232,3 +232,28 @@ def test_server_drain_times_out_then_completes(pw):
             assert st == pw.PW_OK and b == pw.pw_query(g.handle, 10, 20000, 0.05, 200, 4242)
         finally:
             pw.pw_server_destroy(srv)
+
+
+def test_server_tune_keeps_results(pw):
+    """pw_server_tune times every walk-kernel policy on a sample and keeps the
+    fastest; estimates after tuning equal the batch entry point's, and the
+    policies it timed all produced the batch's estimates too (it polls them)."""
+    h = barabasi_albert(20_000, 5, 21)
+    with pw.Graph(h.row_ptr, h.col_idx) as g:
+        s, t = uniform_pairs(h.n, 12, 960)
+        seeds = query_seeds(12, 961)
+        want, st = pw.pw_query_batch(g.handle, s, t, 0.2, 40, seeds)
+        assert np.all(st == 0)
+        pw.pw_autotune(g.handle, s[:4], t[:4], 0.2, 40, seeds[:4])
+        srv = pw.pw_server_create(g.handle, None, 1 << 26)
+        try:
+            r = pw.pw_server_tune(srv, s[:6], t[:6], 0.2, 40, seeds[:6])
+            assert r["policy"] in (0, 1, 2, 3)
+            assert all(r["queries_per_s"][p] > 0 for p in (0, 1, 2, 3))
+            assert r["queries_per_s"][r["policy"]] == max(r["queries_per_s"])
+            tk = [pw.pw_server_submit(srv, int(s[i]), int(t[i]), 0.2, 40, int(seeds[i])) for i in range(12)]
+            pw.pw_server_drain(srv, 60000)
+            got = [pw.pw_server_poll(srv, x)[1] for x in tk]
+        finally:
+            pw.pw_server_destroy(srv)
+        np.testing.assert_array_equal(got, want)
