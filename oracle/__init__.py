@@ -31,7 +31,7 @@ _SRC = os.path.join(_HERE, "walker.c")
 _lock = threading.Lock()
 _lib = None
 
-MODE_PILOT, MODE_THEORY, MODE_SCALED, MODE_FIXED = 0, 1, 2, 3
+MODE_PILOT, MODE_THEORY, MODE_SCALED, MODE_FIXED, MODE_ADAPTIVE = 0, 1, 2, 3, 4
 TAG_WALK, TAG_WALK_PILOT, TAG_PROBE, TAG_PROBE_PILOT = 1, 2, 3, 4
 
 
@@ -60,11 +60,13 @@ class BudgetCfg(ctypes.Structure):
         ("G", ctypes.c_uint64),
         ("R", ctypes.c_uint64),
         ("R_max", ctypes.c_uint64),
+        ("z", ctypes.c_double),
     ]
 
 
-def budget_cfg(mode=MODE_PILOT, delta=0.01, c_B=0.0, c_R=0.0, B=0, G=0, R=0, R_max=0, K0=0, R0=0) -> BudgetCfg:
-    return BudgetCfg(mode, K0, R0, delta, c_B, c_R, B, G, R, R_max)
+def budget_cfg(mode=MODE_PILOT, delta=0.01, c_B=0.0, c_R=0.0, B=0, G=0, R=0, R_max=0, K0=0, R0=0,
+               z=0.0) -> BudgetCfg:
+    return BudgetCfg(mode, K0, R0, delta, c_B, c_R, B, G, R, R_max, z)
 
 
 def _configure(L):
@@ -99,6 +101,9 @@ def _configure(L):
     L.orc_pilot_u.argtypes = [i64p, i32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                               ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, fp]
     L.orc_pilot_u.restype = ctypes.c_int
+    L.orc_adaptive_B.argtypes = [dp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.orc_adaptive_B.restype = ctypes.c_uint64
     L.orc_exact_sum_f32.argtypes = [fp, ctypes.c_int64, ctypes.c_int]
     L.orc_exact_sum_f32.restype = ctypes.c_double
     L.orc_max_threads.argtypes = []
@@ -301,6 +306,14 @@ def exact_sum_f32(u, square: bool = False) -> float:
     rounded once to the nearest double."""
     u = np.ascontiguousarray(u, dtype=np.float32)
     return float(lib().orc_exact_sum_f32(_ptr(u, ctypes.c_float), u.size, 1 if square else 0))
+
+
+def adaptive_B(q, B1: int, B: int, G: int, eps: float, z: float, d_s: float, d_t: float) -> int:
+    """The ADAPTIVE budget's B* from first-stage values q[0 .. G*B1)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    if q.size < G * B1:
+        raise ValueError("q holds fewer than G*B1 values")
+    return int(lib().orc_adaptive_B(_ptr(q, ctypes.c_double), B1, B, G, eps, z, d_s, d_t))
 
 
 def median_of_means(q, B: int, G: int) -> float:

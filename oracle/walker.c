@@ -347,7 +347,7 @@ double orc_exact_sum_f32(const float* u, int64_t n, int square) {
 /* ---------------------------------------------------------------------------
  * Budget (Algorithm 1 line 1; Eqs. B-value, G-value, R-value, K-value).
  * ------------------------------------------------------------------------- */
-enum { ORC_PILOT = 0, ORC_THEORY = 1, ORC_SCALED = 2, ORC_FIXED = 3 };
+enum { ORC_PILOT = 0, ORC_THEORY = 1, ORC_SCALED = 2, ORC_FIXED = 3, ORC_ADAPTIVE = 4 };
 
 typedef struct {
   int32_t mode;
@@ -355,6 +355,7 @@ typedef struct {
   double delta, c_B, c_R;
   uint64_t B, G, R;   /* FIXED mode */
   uint64_t R_max;
+  double z;           /* ADAPTIVE: normal quantile of the stopping rule */
 } orc_budget_cfg;
 
 /* ceil that forgives the last-place error of expressions such as 448/0.1^2 */
@@ -363,6 +364,7 @@ static double ceil_tol(double x) { return ceil(x * (1.0 - 1e-12)); }
 typedef struct {
   uint64_t B, G, K, R;
   double sigma2_hat, q_bar, theta_hat; /* PILOT diagnostics */
+  uint64_t B1;                         /* ADAPTIVE: probes per block of the first stage */
 } orc_budget;
 
 static void fill_defaults(const orc_budget_cfg* in, orc_budget_cfg* c) {
@@ -374,7 +376,8 @@ static void fill_defaults(const orc_budget_cfg* in, orc_budget_cfg* c) {
   if (!(c->c_R > 0)) c->c_R = 1.0;
   /* PILOT's c_B default (0.5) is the calibrated reading of the experimental
    * budget, which the paper leaves open; SCALED scales Eq. B-value by c_B = 1. */
-  if (!(c->c_B > 0)) c->c_B = (c->mode == ORC_PILOT) ? 0.5 : 1.0;
+  if (!(c->c_B > 0)) c->c_B = (c->mode == ORC_PILOT || c->mode == ORC_ADAPTIVE) ? 0.5 : 1.0;
+  if (!(c->z > 0)) c->z = 2.2;
 }
 
 /* R of Eq. R-value before the ceiling. */
@@ -445,7 +448,8 @@ static int compute_budget(const int64_t* row_ptr, const int32_t* col_idx, uint64
       out->R = c.R;
       break;
     }
-    case ORC_PILOT: {
+    case ORC_PILOT:
+    case ORC_ADAPTIVE: {
       double B = ceil_tol(c.c_B / (eps * eps));
       out->B = B < 1.0 ? 1 : (uint64_t)B;
       out->G = G;
@@ -475,6 +479,7 @@ static int compute_budget(const int64_t* row_ptr, const int32_t* col_idx, uint64
       out->sigma2_hat = sigma2;
       out->q_bar = q_bar;
       out->theta_hat = theta;
+      out->B1 = (out->B + 3) / 4; /* ceil(B / 4) */
       break;
     }
     default:
@@ -482,6 +487,40 @@ static int compute_budget(const int64_t* row_ptr, const int32_t* col_idx, uint64
   }
   out->K = out->B * out->G;
   return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * ADAPTIVE budget: early stopping per query.  The median of G block means of
+ * B probes each has, for block means that are near normal, a standard error
+ * of sqrt(pi/2) sd(Q) / sqrt(G B) (the asymptotic variance of a sample median
+ * is pi/2 times that of the mean).  After a first stage of B1 = ceil(B/4)
+ * probes per block, sd(Q) and the mean of Q are estimated from those G B1
+ * values, and the query keeps the smallest B at which z standard errors fit
+ * in eps times the estimated distance:
+ *     B* = ceil( (pi/2) z^2 s^2 / (G eps^2 theta^2) ),  B1 <= B* <= B,
+ * theta = max(mean Q, theta_0) with theta_0 of the PILOT budget.  The
+ * second stage runs probes G B1 .. G B* - 1 and the estimate is the median of
+ * the G contiguous blocks of B* probes (Eq. final-estimator).
+ * ------------------------------------------------------------------------- */
+static uint64_t adaptive_B(const double* q, uint64_t B1, uint64_t B, uint64_t G, double eps, double z, double ds,
+                           double dt) {
+  uint64_t K1 = G * B1;
+  double sum = 0.0;
+  for (uint64_t k = 0; k < K1; ++k) sum = sum + q[k];
+  double mean = sum / (double)K1;
+  double ss = 0.0;
+  for (uint64_t k = 0; k < K1; ++k) ss = ss + (q[k] - mean) * (q[k] - mean);
+  double s2 = K1 > 1 ? ss / (double)(K1 - 1) : 0.0;
+  double inv = 1.0 / ds + 1.0 / dt;
+  double theta0 = (1.0 / 8.0) * (1.0 - eps / 2.0) * inv * inv;
+  double theta = mean > theta0 ? mean : theta0;
+  double x = 1.5707963267948966 * z * z * s2; /* (pi/2) z^2 s^2 */
+  x = x / (theta * theta);
+  x = x / ((double)G * eps * eps);
+  double Bs = ceil_tol(x);
+  if (Bs < (double)B1) Bs = (double)B1;
+  if (Bs > (double)B) Bs = (double)B;
+  return (uint64_t)Bs;
 }
 
 /* ---------------------------------------------------------------------------
@@ -531,13 +570,38 @@ int orc_query(const int64_t* row_ptr, const int32_t* col_idx, int64_t n, int64_t
     pilot_out[0] = bud.sigma2_hat; pilot_out[1] = bud.q_bar; pilot_out[2] = bud.theta_hat;
   }
   double* q = q_out ? q_out : (double*)calloc(bud.K ? bud.K : 1, sizeof(double));
-  for (uint64_t k = 0; k < bud.K; ++k) {
-    q[k] = probe_q(row_ptr, col_idx, (uint64_t)n, s, t, L, seed, (uint32_t)k, bud.R, ORC_TAG_PROBE, ORC_TAG_WALK,
-                   u_out ? u_out + k * bud.R : NULL, NULL, NULL, visits);
+  uint64_t K = bud.K, B = bud.B;
+  if (cfg->mode == ORC_ADAPTIVE) { /* first stage, then the stopping rule */
+    orc_budget_cfg c;
+    fill_defaults(cfg, &c);
+    uint64_t K1 = bud.G * bud.B1;
+    for (uint64_t k = 0; k < K1; ++k)
+      q[k] = probe_q(row_ptr, col_idx, (uint64_t)n, s, t, L, seed, (uint32_t)k, bud.R, ORC_TAG_PROBE, ORC_TAG_WALK,
+                     u_out ? u_out + k * bud.R : NULL, NULL, NULL, visits);
+    B = adaptive_B(q, bud.B1, bud.B, bud.G, eps, c.z, (double)(row_ptr[s + 1] - row_ptr[s]),
+                   (double)(row_ptr[t + 1] - row_ptr[t]));
+    K = bud.G * B;
+    for (uint64_t k = K1; k < K; ++k)
+      q[k] = probe_q(row_ptr, col_idx, (uint64_t)n, s, t, L, seed, (uint32_t)k, bud.R, ORC_TAG_PROBE, ORC_TAG_WALK,
+                     u_out ? u_out + k * bud.R : NULL, NULL, NULL, visits);
+    if (budget_out) {
+      budget_out[0] = B;
+      budget_out[2] = K;
+    }
+  } else {
+    for (uint64_t k = 0; k < K; ++k)
+      q[k] = probe_q(row_ptr, col_idx, (uint64_t)n, s, t, L, seed, (uint32_t)k, bud.R, ORC_TAG_PROBE, ORC_TAG_WALK,
+                     u_out ? u_out + k * bud.R : NULL, NULL, NULL, visits);
   }
-  *beta_hat = median_of_means(q, bud.B, bud.G);
+  *beta_hat = median_of_means(q, B, bud.G);
   if (!q_out) free(q);
   return 0;
+}
+
+/* The ADAPTIVE stopping rule on given first-stage values (tests pin it directly). */
+uint64_t orc_adaptive_B(const double* q, uint64_t B1, uint64_t B, uint64_t G, double eps, double z, double ds,
+                        double dt) {
+  return adaptive_B(q, B1, B, G, eps, z, ds, dt);
 }
 
 /* Median of the G block means of q[0 .. B*G) (tests pin it directly). */

@@ -39,6 +39,10 @@ MUTANTS = {
     "sum_no_sticky": ("(rem == half && (sticky || (mant & 1)))", "(rem == half && (mant & 1))"),
     # S2 accumulated from |U_p| instead of U_p^2
     "s2_not_squared": ("exact_add(&A2, u * u);", "exact_add(&A2, fabs(u));"),
+    # ADAPTIVE stopping rule without the pi/2 variance factor of the median
+    "adaptive_no_median_factor": ("double x = 1.5707963267948966 * z * z * s2;", "double x = z * z * s2;"),
+    # ADAPTIVE stopping rule with the biased (divide by K1) variance
+    "adaptive_biased_variance": ("double s2 = K1 > 1 ? ss / (double)(K1 - 1) : 0.0;", "double s2 = ss / (double)K1;"),
     # theta not floored by theta_0 (the floor from the proof of Theorem 3.8)
     "theta_unfloored": ("double theta = q_bar > theta0 ? q_bar : theta0;", "double theta = q_bar;"),
 }
@@ -79,6 +83,10 @@ def _run_pins(g_tiny):
         ("pilot_accuracy", lambda: walker_pins.test_pilot_accuracy_problem_1(None, g_tiny)),
         ("median_golden", lambda: walker_pins.test_median_of_means_golden(None)),
         ("exact_sum_ties", lambda: walker_pins.test_exact_sum_ties_and_edges(None)),
+        ("adaptive_golden", lambda: walker_pins.test_adaptive_rule_golden(None)),
+        ("adaptive_rule", lambda: walker_pins.test_adaptive_budget_stopping_rule(None, g_tiny, 3, 77, 0.2, 32, 12345)),
+        ("adaptive_rule_2", lambda: walker_pins.test_adaptive_budget_stopping_rule(None, g_tiny, 10, 190, 0.1, 8,
+                                                                                   99)),
         ("even_G_query", lambda: walker_pins.test_even_G_query_takes_middle_pair(None, g_tiny)),
         ("pilot_statistics", lambda: walker_pins.test_pilot_statistics_from_replicas(None, g_tiny, 3, 77, 32, 12345,
                                                                                      0.2)),
