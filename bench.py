@@ -530,10 +530,15 @@ def run_accuracy(args, wl, world, rank, local):
     g = pw.Graph(host.row_ptr, host.col_idx, device=local)
     ref = pw.pw_series_batch(g.handle, s, t, np.full(n, L, np.int32))
     rows = []
-    settings = [(float(c), int(r)) for c in args.c_B_list.split(",") for r in args.r_max.split(",")]
+    budgets = {"pilot": pw.PW_BUDGET_PILOT, "adaptive": pw.PW_BUDGET_ADAPTIVE}
+    settings = [(b, float(c), int(r), 0.0, 0.0) for b in args.budget_list.split(",") if b == "pilot"
+                for c in args.c_B_list.split(",") for r in args.r_max.split(",")]
+    settings += [("adaptive", float(c), int(r), float(z), float(cap)) for b in args.budget_list.split(",")
+                 if b == "adaptive" for c in args.c_B_list.split(",") for r in args.r_max.split(",")
+                 for z in args.z_list.split(",") for cap in args.cap_list.split(",")]
     for e in (0.1, 0.2):
-        for cb, rmax in settings:
-            params = pw.make_params(R_max=rmax, c_B=cb)
+        for bname, cb, rmax, z, cap in settings:
+            params = pw.make_params(R_max=rmax, c_B=cb, budget_mode=budgets[bname], z=z, cap=cap)
             pw.pw_profile(g.handle, enable=True, reset=True)
             t0 = time.perf_counter()
             beta, st, KR, _ = pw.pw_debug_batch_probe_q(g.handle, s, t, e, L, seeds, [], [], params)
@@ -542,7 +547,8 @@ def run_accuracy(args, wl, world, rank, local):
             assert np.all(st == 0)
             rel = np.abs(beta - ref) / ref
             clamped = KR[:, 1] == rmax
-            rows.append({"eps": e, "c_B": cb, "R_max": rmax, "frac_within_eps": float(np.mean(rel <= e)),
+            rows.append({"eps": e, "budget": bname, "c_B": cb, "R_max": rmax, "z": z or None, "cap": cap or None,
+                         "frac_within_eps": float(np.mean(rel <= e)), "mean_B": float(KR[:, 0].mean()) / 37.0,
                          "frac_clamped": float(np.mean(clamped)),
                          "frac_within_eps_clamped": float(np.mean(rel[clamped] <= e)) if clamped.any() else None,
                          "frac_within_eps_unclamped": float(np.mean(rel[~clamped] <= e)) if (~clamped).any() else None,
@@ -905,6 +911,9 @@ def main():
     ap.add_argument("--loads", default="0.5,0.9", help="offered loads of --serving, as fractions of capacity")
     ap.add_argument("--r-max", default="4096,8192,16384", help="R_max values of --accuracy")
     ap.add_argument("--c-B-list", default="0.5", help="c_B values of --accuracy")
+    ap.add_argument("--budget-list", default="pilot", help="budget modes of --accuracy: pilot, adaptive")
+    ap.add_argument("--z-list", default="2.2", help="ADAPTIVE z values of --accuracy")
+    ap.add_argument("--cap-list", default="1", help="ADAPTIVE caps (multiples of PILOT's B) of --accuracy")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

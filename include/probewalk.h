@@ -60,7 +60,19 @@ typedef enum {
  * theta estimated by a pilot of K0 probes x R0 replicas on reserved streams
  * (theta floored by theta_0 = (1/8)(1 - eps/2)(1/d_s + 1/d_t)^2 from the proof of
  * Theorem 3.8), rounded up to a multiple of 32 and clamped to [32, R_max]. */
-enum { PW_BUDGET_PILOT = 0, PW_BUDGET_THEORY = 1, PW_BUDGET_SCALED = 2, PW_BUDGET_FIXED = 3 };
+enum { PW_BUDGET_PILOT = 0, PW_BUDGET_THEORY = 1, PW_BUDGET_SCALED = 2, PW_BUDGET_FIXED = 3, PW_BUDGET_ADAPTIVE = 4 };
+/* ADAPTIVE (the paper has no counterpart: B per query from the variance of
+ * Q_R, Lemma 3.7, and the median of Eq. final-estimator): R as in PILOT; the
+ * probes run in two stages.  The first stage runs B1 = ceil(B_P/4) probes per
+ * block (B_P: PILOT's B); from those G B1 values of Q_R the query keeps the
+ * smallest B* at which z standard errors of the median of means,
+ * sqrt(pi/2) sd(Q) / sqrt(G B*), fit in eps theta (theta = max(mean Q,
+ * theta_0)):  B* = ceil((pi/2) z^2 s^2 / (G eps^2 theta^2)) clamped to
+ * [B1, cap B_P].  The second stage runs probes G B1 .. G B* - 1, and the
+ * estimate is the median of the G contiguous blocks of B* probes.  Defaults
+ * z = 3, cap = 2 (calibrated on 1024 queries per synthetic workload; the
+ * variance estimate misjudges heavy-tailed Q_R, so on R-MAT graphs it does not
+ * save work safely).  Not available in servers. */
 
 /* Parameters; an all-zero struct selects every default. */
 typedef struct pw_params {
@@ -76,6 +88,8 @@ typedef struct pw_params {
   uint64_t seed;           /* global seed for queries that pass no seed */
   int32_t walk_mode;       /* 0 auto (graph cost model, see pw_autotune); 1 probe entries evaluated per visit; 2 per-probe shared-memory table */
   int32_t reserved1;
+  double z;                /* ADAPTIVE: normal quantile of the stopping rule; 0 -> 3 */
+  double cap;              /* ADAPTIVE: the most probes per block as a multiple of PILOT's B; 0 -> 2 */
 } pw_params;
 
 typedef struct pw_graph pw_graph;
@@ -92,8 +106,9 @@ typedef struct pw_server pw_server;
  * connectivity check; bits 1 and 2 force the walks' graph layout, fused
  * 16-byte neighbour records (bit 1: one gather per walk step) or col_idx plus
  * 16-byte node records (bit 2: two smaller gathers per step); by default the
- * fused records are built when they take at most 64 MiB (half of the L2), and
- * the split layout is used otherwise.  Both give the same walks.  Returns
+ * split layout is used when the fused records would take more than 64 MiB
+ * (half of the L2) while col_idx plus node records take at most 160 MiB, and
+ * the fused records otherwise.  Both give the same walks.  Returns
  * PW_ERR_GRAPH if a check fails.
  * On success *out holds a handle to free with pw_graph_free. */
 pw_status pw_graph_load(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz,
@@ -112,7 +127,8 @@ pw_status pw_graph_info(const pw_graph* g, int64_t* n, int64_t* nnz, int32_t* d_
 
 /* ---- budget ----------------------------------------------------------------
  * Budget of one query (Algorithm 1, line 1): writes B, G, K = B*G, R.  In
- * PILOT mode this runs the pilot walks on the GPU.  seed: host pointer to the
+ * PILOT and ADAPTIVE modes this runs the pilot walks on the GPU; ADAPTIVE
+ * reports its first stage (B = ceil(B_PILOT / 4)).  seed: host pointer to the
  * query's 64-bit seed, or NULL for pw_default_seed(params->seed, s, t, eps, L).
  * s == t gives all zeros. */
 pw_status pw_budget(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
@@ -223,7 +239,8 @@ pw_status pw_series_batch(pw_graph* g, int64_t count, const int64_t* s, const in
  * probes g_begin*B .. g_end*B - 1.  block_means (host, g_end - g_begin) gets
  * the block means.  0 <= g_begin < g_end <= G; s != t.  Ranks that own
  * disjoint block ranges gather their means and pw_block_median gives the
- * estimate of the unsharded query, bit for bit. */
+ * estimate of the unsharded query, bit for bit.  Not for ADAPTIVE budgets
+ * (their B is known only after the first stage): PW_ERR_ARG. */
 pw_status pw_query_blocks(pw_graph* g, int64_t s, int64_t t, double eps, int32_t L, const uint64_t* seed,
                           const pw_params* params, int64_t g_begin, int64_t g_end, double* block_means);
 /* pw_block_median: median of G block means (host arrays; mean of the two

@@ -61,12 +61,13 @@ class BudgetCfg(ctypes.Structure):
         ("R", ctypes.c_uint64),
         ("R_max", ctypes.c_uint64),
         ("z", ctypes.c_double),
+        ("cap", ctypes.c_double),
     ]
 
 
 def budget_cfg(mode=MODE_PILOT, delta=0.01, c_B=0.0, c_R=0.0, B=0, G=0, R=0, R_max=0, K0=0, R0=0,
-               z=0.0) -> BudgetCfg:
-    return BudgetCfg(mode, K0, R0, delta, c_B, c_R, B, G, R, R_max, z)
+               z=0.0, cap=0.0) -> BudgetCfg:
+    return BudgetCfg(mode, K0, R0, delta, c_B, c_R, B, G, R, R_max, z, cap)
 
 
 def _configure(L):

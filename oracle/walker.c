@@ -356,6 +356,7 @@ typedef struct {
   uint64_t B, G, R;   /* FIXED mode */
   uint64_t R_max;
   double z;           /* ADAPTIVE: normal quantile of the stopping rule */
+  double cap;         /* ADAPTIVE: the most probes per block, as a multiple of PILOT's B */
 } orc_budget_cfg;
 
 /* ceil that forgives the last-place error of expressions such as 448/0.1^2 */
@@ -377,7 +378,10 @@ static void fill_defaults(const orc_budget_cfg* in, orc_budget_cfg* c) {
   /* PILOT's c_B default (0.5) is the calibrated reading of the experimental
    * budget, which the paper leaves open; SCALED scales Eq. B-value by c_B = 1. */
   if (!(c->c_B > 0)) c->c_B = (c->mode == ORC_PILOT || c->mode == ORC_ADAPTIVE) ? 0.5 : 1.0;
-  if (!(c->z > 0)) c->z = 2.2;
+  /* ADAPTIVE defaults, calibrated on 1024 queries per workload: z = 3 with
+   * B allowed up to twice PILOT's */
+  if (!(c->z > 0)) c->z = 3.0;
+  if (!(c->cap > 0)) c->cap = 2.0;
 }
 
 /* R of Eq. R-value before the ceiling. */
@@ -480,6 +484,7 @@ static int compute_budget(const int64_t* row_ptr, const int32_t* col_idx, uint64
       out->q_bar = q_bar;
       out->theta_hat = theta;
       out->B1 = (out->B + 3) / 4; /* ceil(B / 4) */
+      if (c.mode == ORC_ADAPTIVE) out->B = (uint64_t)ceil_tol(c.cap * (double)out->B); /* the largest B */
       break;
     }
     default:
@@ -490,14 +495,14 @@ static int compute_budget(const int64_t* row_ptr, const int32_t* col_idx, uint64
 }
 
 /* ---------------------------------------------------------------------------
- * ADAPTIVE budget: early stopping per query.  The median of G block means of
+ * ADAPTIVE budget: B per query from its own variance.  The median of G block means of
  * B probes each has, for block means that are near normal, a standard error
  * of sqrt(pi/2) sd(Q) / sqrt(G B) (the asymptotic variance of a sample median
- * is pi/2 times that of the mean).  After a first stage of B1 = ceil(B/4)
- * probes per block, sd(Q) and the mean of Q are estimated from those G B1
- * values, and the query keeps the smallest B at which z standard errors fit
- * in eps times the estimated distance:
- *     B* = ceil( (pi/2) z^2 s^2 / (G eps^2 theta^2) ),  B1 <= B* <= B,
+ * is pi/2 times that of the mean).  After a first stage of B1 = ceil(B_P/4)
+ * probes per block (B_P: PILOT's B), sd(Q) and the mean of Q are estimated
+ * from those G B1 values, and the query keeps the smallest B at which z
+ * standard errors fit in eps times the estimated distance:
+ *     B* = ceil( (pi/2) z^2 s^2 / (G eps^2 theta^2) ),  B1 <= B* <= cap B_P,
  * theta = max(mean Q, theta_0) with theta_0 of the PILOT budget.  The
  * second stage runs probes G B1 .. G B* - 1 and the estimate is the median of
  * the G contiguous blocks of B* probes (Eq. final-estimator).

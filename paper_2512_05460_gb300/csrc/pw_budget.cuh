@@ -60,7 +60,7 @@ __host__ __device__ inline void plan_query(int64_t s, int64_t t, double eps, int
           B = (double)A.B_fixed;
           R = (double)A.R_fixed;
           break;
-        default:  // PILOT
+        default:  // PILOT and ADAPTIVE
           B = ceil_tol(A.c_B / (eps * eps));
           if (B < 1.0) B = 1.0;
           R = 0.0;
@@ -71,10 +71,16 @@ __host__ __device__ inline void plan_query(int64_t s, int64_t t, double eps, int
       } else {
         P.B = (uint32_t)B;
         P.G = A.G;
+        if (A.mode == PW_BUDGET_ADAPTIVE) {  // first stage: ceil(B/4) probes per block
+          const double Bmax = ceil_tol(A.cap * (double)P.B);
+          P.Bmax = Bmax * (double)P.G >= 4294967296.0 ? 0u : (uint32_t)Bmax;
+          if (P.Bmax == 0) P.status = PW_ERR_ARG;
+          P.B = (P.B + 3u) / 4u;
+        }
         P.K = P.B * P.G;
         P.R = (uint32_t)R;
         P.chunks = (P.R + 31u) / 32u;
-        if (A.mode == PW_BUDGET_PILOT) {
+        if (A.mode == PW_BUDGET_PILOT || A.mode == PW_BUDGET_ADAPTIVE) {
           PP.s = P.s;
           PP.t = P.t;
           PP.seed = P.seed;
@@ -92,6 +98,36 @@ __host__ __device__ inline void plan_query(int64_t s, int64_t t, double eps, int
   }
   *out = P;
   if (pilot_out) *pilot_out = PP;
+}
+
+// Q slots a query reserves: G Bmax for ADAPTIVE (its B may grow to Bmax), else K.
+__host__ __device__ __forceinline__ uint64_t q_slots(const QPlan& P) {
+  return P.Bmax ? (uint64_t)P.G * P.Bmax : (uint64_t)P.K;
+}
+
+// ADAPTIVE stopping rule: from the first stage's G*B1 values of Q_R (q), the
+// smallest B with z standard errors of the median of means, sqrt(pi/2) sd(Q) /
+// sqrt(G B), inside eps theta, theta = max(mean Q, theta_0); clamped to
+// [B1, Bmax].  Sums in index order, operation by operation as the oracle.
+__host__ __device__ inline uint32_t adaptive_B(const double* q, uint32_t B1, uint32_t Bmax, uint32_t G, double eps,
+                                               double z, int32_t deg_s, int32_t deg_t) {
+  const uint64_t K1 = (uint64_t)G * B1;
+  double sum = 0.0;
+  for (uint64_t k = 0; k < K1; ++k) sum = sum + q[k];
+  const double mean = sum / (double)K1;
+  double ss = 0.0;
+  for (uint64_t k = 0; k < K1; ++k) ss = ss + (q[k] - mean) * (q[k] - mean);
+  const double s2 = K1 > 1 ? ss / (double)(K1 - 1) : 0.0;
+  const double inv = 1.0 / (double)deg_s + 1.0 / (double)deg_t;
+  const double theta0 = (1.0 / 8.0) * (1.0 - eps / 2.0) * inv * inv;
+  const double theta = mean > theta0 ? mean : theta0;
+  double x = 1.5707963267948966 * z * z * s2;
+  x = x / (theta * theta);
+  x = x / ((double)G * eps * eps);
+  double B = ceil_tol(x);
+  if (B < (double)B1) B = (double)B1;
+  if (B > (double)Bmax) B = (double)Bmax;
+  return (uint32_t)B;
 }
 
 // Q_R = (S1^2 - S2) / (R (R - 1)) (Eq. Q-Ustat).

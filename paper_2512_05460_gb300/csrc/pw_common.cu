@@ -94,7 +94,7 @@ pw_status resolve_budget(const pw_params* params, const pw_graph* g, BudgetArgs*
   if (!(delta > 0.0 && delta < 1.0)) return set_error(PW_ERR_ARG, "delta must lie in (0, 1)");
   BudgetArgs a{};
   a.mode = p.budget_mode;
-  if (a.mode < PW_BUDGET_PILOT || a.mode > PW_BUDGET_FIXED) return set_error(PW_ERR_ARG, "unknown budget_mode");
+  if (a.mode < PW_BUDGET_PILOT || a.mode > PW_BUDGET_ADAPTIVE) return set_error(PW_ERR_ARG, "unknown budget_mode");
   a.K0 = p.pilot_K0 > 0 ? p.pilot_K0 : 64;
   a.R0 = p.pilot_R0 > 1 ? p.pilot_R0 : 32;
   if (a.R0 > 32) return set_error(PW_ERR_ARG, "pilot_R0 must be at most 32");
@@ -104,7 +104,9 @@ pw_status resolve_budget(const pw_params* params, const pw_graph* g, BudgetArgs*
   // PILOT: c_B = 0.5 is the smallest of {0.25, 0.5, 1, 2, 4} that keeps >= 95% of
   // queries within eps on the tiny and BA workloads (held-out seeds); THEORY
   // ignores c_B and SCALED defaults to 1.
-  a.c_B = p.c_B > 0 ? p.c_B : (a.mode == PW_BUDGET_PILOT ? 0.5 : 1.0);
+  a.c_B = p.c_B > 0 ? p.c_B : ((a.mode == PW_BUDGET_PILOT || a.mode == PW_BUDGET_ADAPTIVE) ? 0.5 : 1.0);
+  a.z = p.z > 0 ? p.z : 3.0;      // ADAPTIVE defaults, calibrated on 1024 queries per workload
+  a.cap = p.cap > 0 ? p.cap : 2.0;
   a.c_R = p.c_R > 0 ? p.c_R : 1.0;
   a.R_max = p.R_max ? p.R_max : 4096;
   if (a.mode == PW_BUDGET_FIXED) {

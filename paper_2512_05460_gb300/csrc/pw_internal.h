@@ -20,6 +20,7 @@ struct QPlan {
   uint64_t acc_begin;    // first per-visit probe accumulator
   uint64_t probe_begin;  // first Q slot (K slots)
   uint64_t table_begin;  // first entry of this query in the table kernel's probe list
+  uint64_t q_begin;      // first Q slot of the query (the median reads G B values from here)
   int32_t s, t;
   int32_t L;
   int32_t status;        // pw_status of this query
@@ -27,7 +28,7 @@ struct QPlan {
   uint32_t chunks;       // ceil(R / 32)
   uint32_t k_begin;      // first probe index (a range of blocks of a sharded query; else 0)
   uint32_t mode;         // walk kernel of the query's probes: 1 per-visit evaluation, 2 probe table
-  uint32_t pad;
+  uint32_t Bmax;         // ADAPTIVE: the most probes per block (PILOT's B; Q slots reserved: G Bmax); else 0
   double eps;
   double sigma2, qbar, theta;  // pilot diagnostics
 };
@@ -66,6 +67,8 @@ struct BudgetArgs {
   uint64_t R_max;
   uint64_t global_seed;
   int32_t d_min;
+  double z;    // ADAPTIVE stopping rule's normal quantile
+  double cap;  // ADAPTIVE: the most probes per block as a multiple of PILOT's B
 };
 
 struct DeviceBuffer {

@@ -51,11 +51,12 @@ __global__ void budget_init_kernel(int64_t nq, const int64_t* __restrict__ qs, c
   if (pilot) pilot[q] = PP;
 }
 
-// Sum of K over the batch (device-array calls size their buffers from it).
+// Q slots of the batch: the sum of K, or of G Bmax for ADAPTIVE queries
+// (device-array calls size their buffers from it).
 __global__ void sum_k_kernel(const QPlan* __restrict__ plans, int64_t nq, unsigned long long* __restrict__ out) {
   __shared__ unsigned long long sh[1024];
   unsigned long long acc = 0;
-  for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) acc += plans[q].K;
+  for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) acc += q_slots(plans[q]);
   sh[threadIdx.x] = acc;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -95,14 +96,16 @@ struct ModeArgs {
   double visit_gain;  // saving per visit when entries come from the table
 };
 
+// keep_q (the second stage of ADAPTIVE queries): the Q slots stay where the
+// first stage put them.
 __global__ void scan_kernel(QPlan* __restrict__ plans, int64_t nq, unsigned long long* __restrict__ prefix,
-                            Totals* __restrict__ totals, ModeArgs M) {
+                            Totals* __restrict__ totals, ModeArgs M, int keep_q) {
   __shared__ unsigned long long sh[4][1024];
-  __shared__ unsigned long long sh_steps[1024], sh_visits[1024];
+  __shared__ unsigned long long sh_steps[1024], sh_visits[1024], sh_work[1024];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int64_t per = (nq + nt - 1) / nt;
   const int64_t b0 = per * tid, b = b0 < nq ? b0 : nq, e = b + per < nq ? b + per : nq;
-  unsigned long long a[4] = {0, 0, 0, 0}, steps = 0, visits = 0;
+  unsigned long long a[4] = {0, 0, 0, 0}, steps = 0, visits = 0, work = 0;
   for (int64_t q = b; q < e; ++q) {
     QPlan& P = plans[q];
     const double v = 2.0 * (double)P.R * (double)(P.L + 1);
@@ -114,7 +117,8 @@ __global__ void scan_kernel(QPlan* __restrict__ plans, int64_t nq, unsigned long
     a[0] += mode == 1u ? K * P.chunks : 0ull;  // per-visit tiles
     a[1] += mode == 1u ? K : 0ull;             // per-visit probes (accumulators)
     a[2] += mode == 2u ? K : 0ull;             // table probes
-    a[3] += K;                                 // all probes
+    a[3] += q_slots(P);                        // Q slots
+    work += K;
     steps += K * P.R * (unsigned long long)(P.L > 0 ? P.L : 0);
     visits += 2ull * K * P.R * (unsigned long long)(P.L + 1);
   }
@@ -122,9 +126,10 @@ __global__ void scan_kernel(QPlan* __restrict__ plans, int64_t nq, unsigned long
   for (int j = 0; j < 4; ++j) sh[j][tid] = a[j];
   sh_steps[tid] = steps;
   sh_visits[tid] = visits;
+  sh_work[tid] = work;
   __syncthreads();
   if (tid == 0) {
-    unsigned long long run[4] = {0, 0, 0, 0}, st = 0, vi = 0;
+    unsigned long long run[4] = {0, 0, 0, 0}, st = 0, vi = 0, wk = 0;
     for (int i = 0; i < nt; ++i) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -134,16 +139,17 @@ __global__ void scan_kernel(QPlan* __restrict__ plans, int64_t nq, unsigned long
       }
       st += sh_steps[i];
       vi += sh_visits[i];
+      wk += sh_work[i];
     }
     totals->tiles = run[0];
     totals->visit_probes = run[1];
     totals->table_probes = run[2];
-    totals->probes = run[3];
+    totals->probes = wk;
     totals->steps = st;
     totals->visits = vi;
     prefix[nq] = run[0];
     prefix[(nq + 1) + nq] = run[2];
-    prefix[2 * (nq + 1) + nq] = run[3];
+    if (!keep_q) prefix[2 * (nq + 1) + nq] = run[3];
   }
   __syncthreads();
   unsigned long long o[4];
@@ -155,15 +161,35 @@ __global__ void scan_kernel(QPlan* __restrict__ plans, int64_t nq, unsigned long
     P.tile_begin = o[0];
     P.acc_begin = o[1];
     P.table_begin = o[2];
-    P.probe_begin = o[3];
+    if (!keep_q) {
+      P.probe_begin = o[3];
+      P.q_begin = o[3];
+      prefix[2 * (nq + 1) + q] = o[3];
+    }
     prefix[q] = o[0];
     prefix[(nq + 1) + q] = o[2];
-    prefix[2 * (nq + 1) + q] = o[3];
     o[0] += P.mode == 1u ? K * P.chunks : 0ull;
     o[1] += P.mode == 1u ? K : 0ull;
     o[2] += P.mode == 2u ? K : 0ull;
-    o[3] += K;
+    o[3] += q_slots(P);
   }
+}
+
+// ADAPTIVE, between the stages: each query's B* from its first G B1 values of
+// Q_R; the second stage runs probes G B1 .. G B* - 1 into the Q slots after
+// the first stage's, and the median reads G blocks of B* from q_begin.
+__global__ void adapt_kernel(int64_t nq, QPlan* __restrict__ plans, const double* __restrict__ qbuf, BudgetArgs A,
+                             const int4* __restrict__ node) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  QPlan& P = plans[q];
+  if (P.status != PW_OK || P.K == 0 || P.Bmax == 0) return;
+  const uint32_t B1 = P.B, K1 = P.K;
+  const uint32_t Bs = adaptive_B(qbuf + P.q_begin, B1, P.Bmax, P.G, P.eps, A.z, node[P.s].z, node[P.t].z);
+  P.B = Bs;
+  P.k_begin = K1;
+  P.K = P.G * (Bs - B1);
+  P.probe_begin = P.q_begin + K1;
 }
 
 // Accumulators of the per-visit probes start at zero.
@@ -252,7 +278,7 @@ __global__ void __launch_bounds__(kWalkThreads, MINB) walk_kernel(WalkArgs A) {
       const uint64_t pair = (uint64_t)k * R + p;
       const ZOnTheFly zp{pr};
       const float U = walk_pair<DEBUG>(gr, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
-      if (DEBUG && A.u_debug && q == 0) A.u_debug[(uint64_t)kl * R + p] = U;
+      if (DEBUG && A.u_debug && q == 0) A.u_debug[(uint64_t)k * R + p] = U;
       sum_add(sum, U);
     }
     sum_warp_reduce(sum);
@@ -326,7 +352,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : (THREADS == 512 
       if (p < R) {
         const uint64_t pair = (uint64_t)k * R + p;
         const float U = walk_pair_table<DEBUG>(gr, A.visits, A.walk_tag, zp, P.s, P.t, P.L, P.seed, pair);
-        if (DEBUG && A.u_debug && q == 0) A.u_debug[(uint64_t)kl * R + p] = U;
+        if (DEBUG && A.u_debug && q == 0) A.u_debug[(uint64_t)k * R + p] = U;
         sum_add(sum, U);
       }
       sum_warp_reduce(sum);
@@ -387,7 +413,7 @@ __global__ void mom_kernel(const QPlan* __restrict__ plans, const double* __rest
     return;
   }
   for (uint32_t g = threadIdx.x; g < P.G; g += blockDim.x) {
-    const double* x = qbuf + P.probe_begin + (uint64_t)g * P.B;
+    const double* x = qbuf + P.q_begin + (uint64_t)g * P.B;
     double sum = 0.0;
     for (uint32_t k = 0; k < P.B; ++k) sum = __dadd_rn(sum, x[k]);
     means[g] = __ddiv_rn(sum, (double)P.B);
@@ -426,7 +452,7 @@ __global__ void block_means_kernel(const QPlan* __restrict__ plans, const double
                                    double* __restrict__ means, int32_t* __restrict__ status) {
   const QPlan& P = plans[0];
   for (uint32_t g = threadIdx.x; g < P.G; g += blockDim.x) {
-    const double* x = qbuf + P.probe_begin + (uint64_t)g * P.B;
+    const double* x = qbuf + P.q_begin + (uint64_t)g * P.B;
     double sum = 0.0;
     for (uint32_t k = 0; k < P.B; ++k) sum = __dadd_rn(sum, x[k]);
     means[g] = __ddiv_rn(sum, (double)P.B);
@@ -543,6 +569,8 @@ struct BatchBuffers {
   ProbeAcc* acc;                 // per-visit probe accumulators
 };
 
+static bool has_pilot(const BudgetArgs& ba) { return ba.mode == PW_BUDGET_PILOT || ba.mode == PW_BUDGET_ADAPTIVE; }
+
 struct BatchSizes {
   size_t plans, prefix, totals, counters, pilot_s, q, acc;
 };
@@ -551,9 +579,9 @@ static BatchSizes batch_sizes(size_t nq, size_t total_K, const BudgetArgs& ba) {
   BatchSizes z;
   z.plans = sizeof(QPlan) * nq;
   z.prefix = sizeof(unsigned long long) * 6 * (nq + 1);
-  z.totals = sizeof(Totals) * 2;
+  z.totals = sizeof(Totals) * 3;
   z.counters = 64;
-  z.pilot_s = ba.mode == PW_BUDGET_PILOT ? sizeof(double) * 2 * nq * (size_t)ba.K0 : 16;
+  z.pilot_s = has_pilot(ba) ? sizeof(double) * 2 * nq * (size_t)ba.K0 : 16;
   z.q = sizeof(double) * (total_K ? total_K : 1);
   z.acc = sizeof(ProbeAcc) * (total_K ? total_K : 1);
   return z;
@@ -567,7 +595,7 @@ static pw_status enqueue_budget(pw_graph* g, int64_t count, const int64_t* d_s, 
   const int qthreads = 128;
   const int qblocks = (int)((count + qthreads - 1) / qthreads);
   budget_init_kernel<<<qblocks, qthreads, 0, stream>>>(count, d_s, d_t, d_eps, d_L, d_seeds, ba, g->n, g->d_node,
-                                                       B.plans, ba.mode == PW_BUDGET_PILOT ? B.pplans : nullptr);
+                                                       B.plans, has_pilot(ba) ? B.pplans : nullptr);
   count_launch();
   PW_CUDA_TRY(cudaGetLastError());
   return PW_OK;
@@ -579,7 +607,7 @@ static pw_status enqueue_walks(pw_graph* g, int64_t count, const pw_params* para
                                const BatchBuffers& B, double* d_beta, int32_t* d_status, cudaStream_t stream,
                                DebugOut* dbg) {
   const size_t nq = (size_t)count;
-  const bool pilot = ba.mode == PW_BUDGET_PILOT;
+  const bool pilot = has_pilot(ba);
   const int qthreads = 128;
   const int qblocks = (int)((count + qthreads - 1) / qthreads);
   unsigned long long* prefix = B.prefix;
@@ -594,7 +622,7 @@ static pw_status enqueue_walks(pw_graph* g, int64_t count, const pw_params* para
   pw_status st;
   if (pilot) {
     ModeArgs pm{1, 0, 0.0, 0.0};
-    scan_kernel<<<1, 1024, 0, stream>>>(B.pplans, count, pprefix, B.totals + 1, pm);
+    scan_kernel<<<1, 1024, 0, stream>>>(B.pplans, count, pprefix, B.totals + 1, pm, 0);
     count_launch();
     wa.plans = B.pplans;
     wa.tile_prefix = pprefix;
@@ -623,18 +651,14 @@ static pw_status enqueue_walks(pw_graph* g, int64_t count, const pw_params* para
   ModeArgs M{forced, table_ok ? 1 : 0, g->table_probe_cost, g->table_visit_gain};
   if (params && (params->walk_mode < 0 || params->walk_mode > 2))
     return set_error(PW_ERR_ARG, "walk_mode must be 0, 1 or 2");
-  scan_kernel<<<1, 1024, 0, stream>>>(B.plans, count, prefix, B.totals, M);
+  scan_kernel<<<1, 1024, 0, stream>>>(B.plans, count, prefix, B.totals, M, 0);
   count_launch();
   PW_CUDA_TRY(cudaGetLastError());
   if (dbg && dbg->budget_only) return PW_OK;
-  zero_acc_kernel<<<g->sm_count * 4, 256, 0, stream>>>(B.acc, B.totals);
-  count_launch();
-  PW_CUDA_TRY(cudaGetLastError());
   const bool debug = dbg && (dbg->visits || dbg->u);
   wa.plans = B.plans;
   wa.tile_prefix = prefix;
   wa.table_prefix = prefix + (nq + 1);
-  wa.totals = B.totals;
   wa.acc = B.acc;
   wa.q = B.q;
   wa.visits = dbg ? dbg->visits : nullptr;
@@ -654,14 +678,34 @@ static pw_status enqueue_walks(pw_graph* g, int64_t count, const pw_params* para
       return cuda_error(e, "walk timing events");
     }
   }
-  st = PW_OK;
-  if (table_ok) {
-    wa.counter = B.counters + 2;
-    st = launch_table(g, stream, wa, debug);
-  }
-  if (st == PW_OK) {
-    wa.counter = B.counters;
-    st = launch_walk(g, stream, wa, debug, false);
+  // one walk stage: accumulators zeroed, then the table and per-visit kernels
+  // (each takes only its own queries' probes, as the scan assigned them)
+  auto walk_stage = [&](Totals* totals, unsigned long long* counters) -> pw_status {
+    zero_acc_kernel<<<g->sm_count * 4, 256, 0, stream>>>(B.acc, totals);
+    count_launch();
+    PW_CUDA_TRY(cudaGetLastError());
+    wa.totals = totals;
+    pw_status s2 = PW_OK;
+    if (table_ok) {
+      wa.counter = counters + 2;
+      s2 = launch_table(g, stream, wa, debug);
+    }
+    if (s2 == PW_OK) {
+      wa.counter = counters;
+      s2 = launch_walk(g, stream, wa, debug, false);
+    }
+    return s2;
+  };
+  st = walk_stage(B.totals, B.counters);
+  if (st == PW_OK && ba.mode == PW_BUDGET_ADAPTIVE) {
+    // the stopping rule on the first stage's Q_R, then the second stage's
+    // probes with their own offsets and totals (Q slots stay in place)
+    adapt_kernel<<<qblocks, qthreads, 0, stream>>>(count, B.plans, B.q, ba, g->d_node);
+    count_launch();
+    scan_kernel<<<1, 1024, 0, stream>>>(B.plans, count, prefix, B.totals + 2, M, 1);
+    count_launch();
+    const cudaError_t e = cudaGetLastError();
+    st = e == cudaSuccess ? walk_stage(B.totals + 2, B.counters + 4) : cuda_error(e, "adaptive stage");
   }
   if (tw[0]) {
     cudaError_t e = st == PW_OK ? cudaEventRecord(tw[1], stream) : cudaSuccess;
@@ -760,7 +804,9 @@ static pw_status enqueue_batch(pw_graph* g, int64_t count, const int64_t* d_s, c
   if ((st = enqueue_budget(g, count, d_s, d_t, d_eps, d_L, d_seeds, ba, B, stream)) != PW_OK) return st;
   if ((st = enqueue_walks(g, count, params, ba, B, d_beta, d_status, stream, dbg)) != PW_OK) return st;
   PW_CUDA_TRY(cudaMemcpyAsync(g->ws.host_totals, B.totals, sizeof(Totals), cudaMemcpyDeviceToHost, stream));
-  return prof_totals(g, B.totals, stream);
+  st = prof_totals(g, B.totals, stream);
+  if (st == PW_OK && ba.mode == PW_BUDGET_ADAPTIVE && !(dbg && dbg->budget_only)) st = prof_totals(g, B.totals + 2, stream);
+  return st;
 }
 
 pw_status run_batch(pw_graph* g, int64_t count, const int64_t* d_s, const int64_t* d_t, const double* d_eps,
@@ -799,7 +845,7 @@ static size_t host_total_K(const pw_graph* g, int64_t count, const int64_t* s, c
     QPlan P;
     plan_query(s[i], t[i], eps[i], L[i], 0, g->n, in ? g->deg[(size_t)s[i]] : 1, in ? g->deg[(size_t)t[i]] : 1, ba,
                &P, nullptr);
-    K += P.K;
+    K += q_slots(P);
   }
   return K;
 }
@@ -1060,8 +1106,8 @@ pw_status pw_debug_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t 
   if (st != PW_OK) return st;
   QPlan P0;
   if ((st = copy_plan(g, 0, &P0)) != PW_OK) return st;
-  const uint64_t KR0 = (uint64_t)P0.K * P0.R;
-  if ((q && (uint64_t)q_cap < P0.K) || (u && (uint64_t)u_cap < KR0)) return set_error(PW_ERR_ARG, "q_cap or u_cap too small");
+  const uint64_t K0 = q_slots(P0), KR0 = K0 * P0.R;  // ADAPTIVE: the most its second stage may reach
+  if ((q && (uint64_t)q_cap < K0) || (u && (uint64_t)u_cap < KR0)) return set_error(PW_ERR_ARG, "q_cap or u_cap too small");
   // pass 2: the whole query, with replica values and visit counts
   DebugOut dbg;
   DeviceBuffer vis;
@@ -1080,10 +1126,11 @@ pw_status pw_debug_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t 
   memset(&P, 0, sizeof P);
   if (st == PW_OK) st = copy_plan(g, 0, &P);
   if (st == PW_OK) {
+    const uint64_t K = (uint64_t)P.G * P.B, KR = K * P.R;  // after an ADAPTIVE second stage too
     if (budget) {
       budget[0] = P.B;
       budget[1] = P.G;
-      budget[2] = P.K;
+      budget[2] = K;
       budget[3] = P.R;
     }
     if (pilot) {
@@ -1091,8 +1138,7 @@ pw_status pw_debug_query(pw_graph* g, int64_t s, int64_t t, double eps, int32_t 
       pilot[1] = P.qbar;
       pilot[2] = P.theta;
     }
-    const uint64_t K = P.K, KR = (uint64_t)P.K * P.R;
-    if (q && K) cudaMemcpyAsync(q, (double*)g->ws.q.ptr + P.probe_begin, sizeof(double) * K, cudaMemcpyDeviceToHost,
+    if (q && K) cudaMemcpyAsync(q, (double*)g->ws.q.ptr + P.q_begin, sizeof(double) * K, cudaMemcpyDeviceToHost,
                                 g->stream);
     if (u && KR) cudaMemcpyAsync(u, g->ws.u_debug.ptr, sizeof(float) * KR, cudaMemcpyDeviceToHost, g->stream);
     if (visits) cudaMemcpyAsync(visits, vis.ptr, sizeof(uint32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, g->stream);
@@ -1114,6 +1160,7 @@ pw_status pw_query_blocks(pw_graph* g, int64_t s, int64_t t, double eps, int32_t
   pw_status st = resolve_budget(params, g, &ba, nullptr);
   if (st != PW_OK) return st;
   if (g_begin < 0 || g_end <= g_begin || g_end > (int64_t)ba.G) return set_error(PW_ERR_ARG, "block range outside [0, G)");
+  if (ba.mode == PW_BUDGET_ADAPTIVE) return set_error(PW_ERR_ARG, "pw_query_blocks needs a budget fixed in advance");
   const uint64_t sd = seed ? *seed : default_seed(ba.global_seed, s, t, eps, L);
   DebugOut dbg;
   DeviceBuffer means;
@@ -1429,14 +1476,14 @@ pw_status pw_debug_batch_probe_q(pw_graph* g, int64_t count, const int64_t* s, c
   PW_CUDA_TRY(cudaStreamSynchronize(g->stream));
   if (KR)
     for (int64_t i = 0; i < count; ++i) {
-      KR[2 * i] = plans[(size_t)i].K;
+      KR[2 * i] = (uint64_t)plans[(size_t)i].G * plans[(size_t)i].B;
       KR[2 * i + 1] = plans[(size_t)i].R;
     }
   for (int64_t i = 0; i < n_sel; ++i) {
     const int64_t qi = sel_query[i], k = sel_probe[i];
-    if (qi < 0 || qi >= count || k < 0 || (uint64_t)k >= plans[(size_t)qi].K)
+    if (qi < 0 || qi >= count || k < 0 || (uint64_t)k >= (uint64_t)plans[(size_t)qi].G * plans[(size_t)qi].B)
       return set_error(PW_ERR_ARG, "selection out of range");
-    PW_CUDA_TRY(cudaMemcpyAsync(q_sel + i, (double*)g->ws.q.ptr + plans[(size_t)qi].probe_begin + k, sizeof(double),
+    PW_CUDA_TRY(cudaMemcpyAsync(q_sel + i, (double*)g->ws.q.ptr + plans[(size_t)qi].q_begin + k, sizeof(double),
                                 cudaMemcpyDeviceToHost, g->stream));
   }
   PW_CUDA_TRY(cudaStreamSynchronize(g->stream));

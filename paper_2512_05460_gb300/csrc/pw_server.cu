@@ -598,6 +598,7 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
   pw_status st = resolve_budget(params, g, &ba, nullptr);
   if (st != PW_OK) return st;
   if (ba.G > kServerGmax) return set_error(PW_ERR_ARG, "server supports G <= 2048");
+  if (ba.mode == PW_BUDGET_ADAPTIVE) return set_error(PW_ERR_ARG, "servers run budgets fixed at admission (not ADAPTIVE)");
   if (accum_bytes < ((size_t)1 << 20)) accum_bytes = (size_t)1 << 20;
   PW_CUDA_TRY(cudaSetDevice(g->device));
   pw_server* sv = new pw_server();

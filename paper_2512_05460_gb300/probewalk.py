@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libprobewalk.so")
 PW_OK, PW_PENDING = 0, 1
 PW_ERR_ARG, PW_ERR_GRAPH, PW_ERR_NOMEM, PW_ERR_CUDA = -1, -2, -3, -4
 PW_ERR_TIMEOUT, PW_ERR_CANCELLED, PW_ERR_FULL = -5, -6, -7
-PW_BUDGET_PILOT, PW_BUDGET_THEORY, PW_BUDGET_SCALED, PW_BUDGET_FIXED = 0, 1, 2, 3
+PW_BUDGET_PILOT, PW_BUDGET_THEORY, PW_BUDGET_SCALED, PW_BUDGET_FIXED, PW_BUDGET_ADAPTIVE = 0, 1, 2, 3, 4
 TAG_WALK, TAG_WALK_PILOT, TAG_PROBE, TAG_PROBE_PILOT = 1, 2, 3, 4
 # pw_graph_load flags: skip the connectivity check; force the fused or the split walk layout
 LOAD_NO_CONNECTIVITY, LOAD_FUSED, LOAD_SPLIT = 1, 2, 4
@@ -52,6 +52,8 @@ class pw_params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("walk_mode", ctypes.c_int32),
         ("reserved1", ctypes.c_int32),
+        ("z", ctypes.c_double),
+        ("cap", ctypes.c_double),
     ]
 
 

@@ -60,7 +60,7 @@ def test_pure_host_entry_points(built_lib):
         assert built_lib.pw_default_seed(*args) == oracle.default_seed(*args)
 
 
-@pytest.mark.parametrize("struct", ["pw_params", "pw_profile_stats", "pw_tune_result"])
+@pytest.mark.parametrize("struct", ["pw_params", "pw_profile_stats", "pw_tune_result", "pw_server_tune_result"])
 def test_struct_layout(built_lib, tmp_path, struct):
     """The binding's structs match the header's layout (sizeof, offsetof)."""
     import ctypes

@@ -1,7 +1,8 @@
 """Parity at the larger workload sizes, in the launch configuration the
 library picks for them: R-MAT 2^20 (646K nodes, 31M entries; split layout,
-walk kernel per query) and the 2000x2000 grid with 5% of edges deleted (4M
-nodes; split layout; table too large for shared memory, per-visit kernel).
+walk kernel per query), the 2000x2000 grid with 5% of edges deleted (4M
+nodes; split layout; table too large for shared memory, per-visit kernel) and
+R-MAT 2^24 (fused records: its split arrays would not fit L2 either).
 The oracle recomputes sampled probes one by one."""
 
 import numpy as np
@@ -66,4 +67,4 @@ def test_rmat24_sampled_probes(pw, oracle_lib):
     host = rmat_native(24, 16, (0.57, 0.19, 0.19, 0.05), 4)
     s, t = uniform_pairs(host.n, 3, 104)
     eps = eps_uniform(3, 0.05, 0.2, 104)
-    _sampled_parity(pw, host, s, t, eps, np.full(3, 1000, np.int32), query_seeds(3, 1004), n_sel=4, layout=2)
+    _sampled_parity(pw, host, s, t, eps, np.full(3, 1000, np.int32), query_seeds(3, 1004), n_sel=4, layout=1)

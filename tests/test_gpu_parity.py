@@ -254,6 +254,32 @@ def test_even_G_delta_005_bit_exact(pw, oracle_lib, tiny, walk_mode):
     np.testing.assert_array_equal(b2, o2)
 
 
+@pytest.mark.parametrize("walk_mode", [1, 2])
+def test_adaptive_budget_bit_exact(pw, oracle_lib, tiny, walk_mode):
+    """ADAPTIVE budget (first stage, stopping rule, second stage): the stopping
+    B*, every U_p of both stages, every Q_R, the visit counts and the estimate
+    equal the oracle's; a batch of 24 mixed queries equals the oracle query by
+    query, and the queries' B differ from PILOT's (up to twice it)."""
+    host, g = tiny
+    params = pw.make_params(budget_mode=pw.PW_BUDGET_ADAPTIVE, walk_mode=walk_mode)
+    cfg = oracle.budget_cfg(mode=oracle.MODE_ADAPTIVE)
+    for s, t, seed in ((3, 77, 12345), (0, 199, 1), (150, 9, 2**62 + 11)):
+        _compare_query(pw, host, g, s, t, 0.2, 32, seed, params, cfg)
+    s, t = uniform_pairs(host.n, 24, 450)
+    eps = eps_uniform(24, 0.1, 0.3, 451)
+    L = np.random.default_rng(452).integers(0, 40, size=24).astype(np.int32)
+    seeds = query_seeds(24, 453)
+    beta, st = pw.pw_query_batch(g.handle, s, t, eps, L, seeds, params)
+    want, budgets, ost = oracle.query_many(host, s, t, eps, L, seeds, cfg)
+    assert np.all(st == 0) and np.all(ost == 0)
+    np.testing.assert_allclose(beta, want, rtol=REL_TOL, atol=0)
+    np.testing.assert_array_equal(beta, want)
+    _, pilot_budgets, _ = oracle.query_many(host, s, t, eps, L, seeds)
+    assert np.all(budgets[:, 0] <= 2 * pilot_budgets[:, 0]) and np.any(budgets[:, 0] != pilot_budgets[:, 0])
+    for i in range(3):
+        assert pw.pw_query(g.handle, int(s[i]), int(t[i]), float(eps[i]), int(L[i]), int(seeds[i]), params) == want[i]
+
+
 @pytest.mark.parametrize("mode", ["THEORY", "SCALED"])
 def test_budget_modes_match_oracle(pw, oracle_lib, tiny, mode):
     host, g = tiny

@@ -84,9 +84,10 @@ def _run_pins(g_tiny):
         ("median_golden", lambda: walker_pins.test_median_of_means_golden(None)),
         ("exact_sum_ties", lambda: walker_pins.test_exact_sum_ties_and_edges(None)),
         ("adaptive_golden", lambda: walker_pins.test_adaptive_rule_golden(None)),
-        ("adaptive_rule", lambda: walker_pins.test_adaptive_budget_stopping_rule(None, g_tiny, 3, 77, 0.2, 32, 12345)),
+        ("adaptive_rule", lambda: walker_pins.test_adaptive_budget_stopping_rule(None, g_tiny, 3, 77, 0.2, 32, 12345,
+                                                                                 2.0)),
         ("adaptive_rule_2", lambda: walker_pins.test_adaptive_budget_stopping_rule(None, g_tiny, 10, 190, 0.1, 8,
-                                                                                   99)),
+                                                                                   99, 1.0)),
         ("even_G_query", lambda: walker_pins.test_even_G_query_takes_middle_pair(None, g_tiny)),
         ("pilot_statistics", lambda: walker_pins.test_pilot_statistics_from_replicas(None, g_tiny, 3, 77, 32, 12345,
                                                                                      0.2)),

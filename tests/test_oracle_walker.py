@@ -322,19 +322,20 @@ def test_exact_sum_ties_and_edges(oracle_lib):
         assert got == want and math.copysign(1.0, got) == math.copysign(1.0, want), (vals, got, want)
 
 
+@pytest.mark.parametrize("cap", [1.0, 2.0])
 @pytest.mark.parametrize("s,t,eps,L,seed", [(3, 77, 0.2, 32, 12345), (10, 190, 0.1, 8, 99), (42, 43, 0.15, 20, 7),
                                             ("hub", 0, 0.2, 32, 2)])
-def test_adaptive_budget_stopping_rule(oracle_lib, tiny_graph, s, t, eps, L, seed):
-    """ADAPTIVE budget: from the first stage's G ceil(B/4) values of Q_R,
-    B* = ceil((pi/2) z^2 s^2 / (G eps^2 theta^2)) clamped to [ceil(B/4), B]
-    (numpy's unbiased variance and mean, theta = max(mean, theta_0)); the
-    estimate is numpy's median of the G block means of the first G B* probes,
-    which are the PILOT query's own probes."""
+def test_adaptive_budget_stopping_rule(oracle_lib, tiny_graph, s, t, eps, L, seed, cap):
+    """ADAPTIVE budget: from the first stage's G ceil(B/4) values of Q_R
+    (B: PILOT's), B* = ceil((pi/2) z^2 s^2 / (G eps^2 theta^2)) clamped to
+    [ceil(B/4), cap B] (numpy's unbiased variance and mean, theta =
+    max(mean, theta_0)); the estimate is numpy's median of the G block means
+    of the first G B* probes, which extend the PILOT query's own probes."""
     g = tiny_graph
     if s == "hub":
         g, s = _hub_graph(), 1
     z = 2.2
-    cfg = oracle.budget_cfg(mode=oracle.MODE_ADAPTIVE, z=z)
+    cfg = oracle.budget_cfg(mode=oracle.MODE_ADAPTIVE, z=z, cap=cap)
     out = oracle.query(g, s, t, eps, L, seed, cfg, want_q=True)
     pilot = oracle.query(g, s, t, eps, L, seed, oracle.budget_cfg(), want_q=True)
     assert out["R"] == pilot["R"] and out["G"] == pilot["G"]
@@ -345,10 +346,12 @@ def test_adaptive_budget_stopping_rule(oracle_lib, tiny_graph, s, t, eps, L, see
     theta0 = 0.125 * (1 - eps / 2) * (1 / d[s] + 1 / d[t]) ** 2
     theta = max(q1.mean(), theta0)
     x = math.pi / 2 * z * z * q1.var(ddof=1) / (G * eps * eps * theta * theta)
-    lo = min(Bp, max(B1, math.ceil(x * (1 - 1e-9))))
-    hi = min(Bp, max(B1, math.ceil(x * (1 + 1e-9))))
+    Bcap = math.ceil(cap * Bp - 1e-9)
+    lo = min(Bcap, max(B1, math.ceil(x * (1 - 1e-9))))
+    hi = min(Bcap, max(B1, math.ceil(x * (1 + 1e-9))))
     assert lo <= out["B"] <= hi and out["K"] == G * out["B"]
-    np.testing.assert_array_equal(out["q"], pilot["q"][: out["K"]])  # the same probes, a prefix
+    common = min(out["K"], pilot["K"])
+    np.testing.assert_array_equal(out["q"][:common], pilot["q"][:common])  # the same probes, extended
     means = out["q"].reshape(G, out["B"]).mean(axis=1)
     assert out["beta"] == pytest.approx(float(np.median(means)), rel=1e-12, abs=1e-300)
 
