@@ -59,11 +59,17 @@ SECTOR_BYTES = 32  # one 16-byte neighbour record per transition lives in one 32
 L2_BYTES = 129 << 20
 WALK_KERNEL_NAME = {1: "walk_kernel (per-visit probe evaluation)", 2: "walk_table_kernel (per-probe table)",
                     3: "walk_table_kernel and walk_kernel (walk kernel chosen per query)"}
-# Per-transition DRAM and L2 bytes of a walk kernel from one ncu capture on a
-# small case of the same workload, scaled to a launch by its transitions
-# (filled per (workload, walk kernel) when a capture of the current kernels
-# exists; the line reports null traffic otherwise).
-WALK_TRAFFIC = {}
+# DRAM and L2 traffic of a walk kernel from one ncu capture on a small case of
+# the same workload (null when no capture of the current kernel exists, or
+# when the batch ran both walk kernels).  BA, table kernel, one launch of 8
+# queries (5.2096e9 transitions): dram read+write 16.04 MB + 2.6 KB, the record
+# array read once into L2 whatever the transitions, so the DRAM bytes are not
+# scaled; lts__t_sectors 5.653e9, 1.085 sectors per transition, scaled.
+WALK_TRAFFIC = {
+    ("ba-1e5", 2): {"dram_per_launch": 16.041472e6 + 2560.0, "l2_per_transition": 5652706685 * 32 / 5.2096e9,
+                    "note": "ncu capture of one 8-query launch: DRAM reads are the 16 MB record array, loaded once "
+                            "into L2 (not scaled); L2 sectors scaled by transitions"},
+}
 
 
 def load_peaks():
@@ -822,7 +828,7 @@ def run_ours(args, wl, world, rank, local):
                     "gather_ceiling_kind": "measured in this run: dependent random 16-B gathers uniform over the "
                                            "same record array (pw_debug_gather_peak)"}
     tr = WALK_TRAFFIC.get((args.workload, walk_mode))
-    roofline.update({"traffic": tr and tr["dram_per_transition"] * transitions_per_step,
+    roofline.update({"traffic": tr and tr["dram_per_launch"],
                      "l2_traffic": tr and tr["l2_per_transition"] * transitions_per_step,
                      "traffic_note": tr and tr["note"],
                      "kernel": WALK_KERNEL_NAME[walk_mode],
