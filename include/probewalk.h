@@ -47,7 +47,8 @@ typedef enum {
   PW_ERR_CUDA = -4,      /* a CUDA runtime call failed (message in pw_last_error) */
   PW_ERR_TIMEOUT = -5,   /* a bounded wait expired */
   PW_ERR_CANCELLED = -6, /* server query cancelled or server shut down */
-  PW_ERR_FULL = -7       /* server queue full */
+  PW_ERR_FULL = -7,      /* server queue full */
+  PW_ERR_INTERNAL = -8   /* a self-check failed (pw_server_tune: variants gave different estimates) */
 } pw_status;
 
 /* Budget modes.  THEORY is Algorithm 1's parameter line (Eqs. B-value,
@@ -282,17 +283,24 @@ pw_status pw_server_collect(pw_server* srv, int64_t cap, uint64_t* tickets, doub
  * per-probe shared-memory table of z or evaluating z at each visit; the
  * choice follows a cost model {table cost per probe, saving per visit}.
  * pw_server_tune runs the sample (host arrays as in pw_query_batch; seeds may
- * be NULL) through the server as a burst, once to warm up and once timed,
- * under each policy: 0 the default model (n Feistel passes per table against
- * 2.5 per visit), 1 the graph's model fitted by pw_autotune on the batch
- * kernels (skipped when the graph is untuned), 2 every query per-visit, 3
- * every query with the table (skipped when the table does not fit).  It keeps
- * the fastest and reports each policy's queries/s (0 for a skipped one).
- * Call it on an idle server: the sample's tickets are consumed by the tuner. */
+ * be NULL) through the server as a burst, once to warm up and once timed.
+ * When the graph's probe table fits in shared memory it times each policy:
+ * 0 the default model (n Feistel passes per table against 2.5 per visit), 1
+ * the graph's model fitted by pw_autotune on the batch kernels (skipped when
+ * the graph is untuned), 2 every query per-visit, 3 every query with the
+ * table, and keeps the fastest.  When the table does not fit, every policy
+ * runs the same per-visit jobs; it then times the server kernel at 2 and at 3
+ * resident blocks per SM (the second with fewer registers, some spilled) and
+ * keeps the faster.  Queries/s are reported for each timed case (0 for one
+ * not timed).  The sums being exact, every case must give the same estimates
+ * bit for bit; the tuner compares them and returns PW_ERR_INTERNAL if they
+ * differ.  Call it on an idle server: the sample's tickets are consumed by
+ * the tuner. */
 typedef struct pw_server_tune_result {
-  double queries_per_s[4];
-  int32_t policy;          /* the policy kept */
-  int32_t reserved;
+  double queries_per_s[4];  /* per policy (table servers); [0] the kept variant otherwise */
+  double occupancy_qps[2];  /* per-visit-only servers: at 2 and at 3 blocks/SM */
+  int32_t policy;           /* the policy kept */
+  int32_t occupancy;        /* resident blocks/SM of the kernel kept (4 for the table kernel) */
 } pw_server_tune_result;
 pw_status pw_server_tune(pw_server* srv, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
                          const int32_t* L, const uint64_t* seeds, pw_server_tune_result* out);

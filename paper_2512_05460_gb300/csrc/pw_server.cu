@@ -169,8 +169,10 @@ __device__ __noinline__ float server_walk_visit(const GR gr, uint32_t n, uint32_
 }
 
 // TABLE: the graph's probe table fits in shared memory, so main-stage jobs may
-// use it (4 blocks/SM); without it only per-visit jobs exist and the kernel
-// keeps the registers that path needs (no occupancy cap).
+// use it (4 blocks/SM); without it only per-visit jobs exist and MINB is the
+// occupancy the registers are capped for: 2 blocks/SM (the registers the
+// per-visit path asks for) or 3 (fewer registers, some spilled), whichever
+// pw_server_tune finds faster on the graph.
 // The graph access of the server: fused records, or col_idx plus node records.
 template <class GR>
 __device__ __forceinline__ GR server_graph(const ServerArgs& A);
@@ -183,8 +185,8 @@ __device__ __forceinline__ SplitRecords server_graph<SplitRecords>(const ServerA
   return SplitRecords{A.col, A.node};
 }
 
-template <bool TABLE, class GR>
-__global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(ServerArgs A) {
+template <bool TABLE, class GR, int MINB>
+__global__ void __launch_bounds__(kServerThreads, MINB) server_kernel(ServerArgs A) {
   const GR gr = server_graph<GR>(A);
   extern __shared__ uint32_t smem[];
   uint32_t* tab = smem;
@@ -330,9 +332,14 @@ __global__ void __launch_bounds__(kServerThreads, TABLE ? 4 : 2) server_kernel(S
 }
 
 using ServerFn = void (*)(ServerArgs);
-static ServerFn server_fn(bool table, int layout) {
-  if (layout == 2) return table ? server_kernel<true, SplitRecords> : server_kernel<false, SplitRecords>;
-  return table ? server_kernel<true, FusedRecords> : server_kernel<false, FusedRecords>;
+// minb: 2 or 3 blocks/SM for the per-visit-only kernel (the table kernel is 4)
+static ServerFn server_fn(bool table, int layout, int minb) {
+  if (layout == 2) {
+    if (table) return server_kernel<true, SplitRecords, 4>;
+    return minb == 3 ? server_kernel<false, SplitRecords, 3> : server_kernel<false, SplitRecords, 2>;
+  }
+  if (table) return server_kernel<true, FusedRecords, 4>;
+  return minb == 3 ? server_kernel<false, FusedRecords, 3> : server_kernel<false, FusedRecords, 2>;
 }
 
 struct Request {
@@ -381,7 +388,9 @@ struct pw_server {
   uint64_t host_tail = 0;
   cudaStream_t kstream = nullptr, cstream = nullptr;
   size_t smem = 0;
-  int grid = 0;
+  int minb = 2;      // occupancy variant of the per-visit-only kernel (server_fn)
+  int grid = 0;      // blocks of the persistent kernel: SMs x resident blocks of that variant
+  int grids[2] = {0, 0};  // per-visit-only kernel: grid at minb 2, 3
   double table_probe_cost = 0.0, table_visit_gain = 0.0;  // walk-mode cost model (host copy of d_model)
   double* d_model = nullptr;
   bool kernel_live = false;
@@ -541,8 +550,11 @@ static void worker_loop(pw_server* sv) {
   const ServerArgs args = server_args(sv);
   for (;;) {
     bool idle = true;
+    int minb = 2, grid = 0;
     {
       std::unique_lock<std::mutex> lk(sv->mu);
+      minb = sv->minb;
+      grid = sv->grid;
       const uint32_t before = sv->active;
       collect(sv);
       if (sv->active != before) idle = false;
@@ -564,8 +576,8 @@ static void worker_loop(pw_server* sv) {
         cudaStreamWaitEvent(sv->kstream, ev, 0);
         cudaEventDestroy(ev);
         cudaMemsetAsync(sv->d_ctl + 4, 0, sizeof(unsigned long long), sv->kstream);  // exit flag
-        const ServerFn fn = server_fn(args.table_words > 0, sv->g->layout);
-        fn<<<sv->grid, kServerThreads, sv->smem, sv->kstream>>>(args);
+        const ServerFn fn = server_fn(args.table_words > 0, sv->g->layout, minb);
+        fn<<<grid, kServerThreads, sv->smem, sv->kstream>>>(args);
         count_launch();
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -656,14 +668,19 @@ pw_status pw_server_create(pw_graph* g, const pw_params* params, size_t accum_by
   const size_t tbytes = (sizeof(uint32_t) * (size_t)table_words((uint32_t)g->n) + 15) & ~(size_t)15;
   sv->smem = ubytes + ((tbytes + ubytes <= 200 * 1024) ? tbytes : 0);
   const bool with_table = sv->smem > ubytes;
-  const ServerFn fn = server_fn(with_table, g->layout);
-  if ((e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv->smem)) !=
-      cudaSuccess)
-    return fail(cuda_error(e, "server smem attribute"));
-  int nb = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kServerThreads, sv->smem)) != cudaSuccess)
-    return fail(cuda_error(e, "server occupancy"));
-  sv->grid = g->sm_count * (nb > 0 ? nb : 1);
+  for (int v = 0; v < (with_table ? 1 : 2); ++v) {
+    const ServerFn fn = server_fn(with_table, g->layout, 2 + v);
+    if ((e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv->smem)) !=
+        cudaSuccess)
+      return fail(cuda_error(e, "server smem attribute"));
+    int nb = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kServerThreads, sv->smem)) !=
+        cudaSuccess)
+      return fail(cuda_error(e, "server occupancy"));
+    sv->grids[v] = g->sm_count * (nb > 0 ? nb : 1);
+  }
+  sv->minb = 2;
+  sv->grid = sv->grids[0];
   cudaDeviceSynchronize();
   sv->worker = std::thread(worker_loop, sv);
   *out = sv;
@@ -743,24 +760,13 @@ pw_status pw_server_tune(pw_server* sv, int64_t count, const int64_t* s, const i
   memset(out, 0, sizeof *out);
   pw_graph* g = sv->g;
   const bool table = sv->smem > kServerMeansBytes;
-  // candidate policies {table cost per probe, saving per visit}: the default
-  // model, the graph's batch-fitted model, every query per-visit, every query
-  // on the table (last two only where meaningful)
-  const double cand[4][2] = {{(double)g->n, 2.5}, {g->table_probe_cost, g->table_visit_gain}, {1.0, 0.0}, {0.0, 1.0}};
-  const bool valid[4] = {true, g->tuned != 0, true, table};
-  int best = 0;
   std::vector<uint64_t> tk((size_t)count);
-  for (int c = 0; c < 4; ++c) {
-    if (!valid[c]) continue;
-    {
-      std::lock_guard<std::mutex> lk(sv->mu);
-      sv->table_probe_cost = cand[c][0];
-      sv->table_visit_gain = cand[c][1];
-    }
-    PW_CUDA_TRY(cudaSetDevice(g->device));
-    PW_CUDA_TRY(cudaMemcpy(sv->d_model, cand[c], 2 * sizeof(double), cudaMemcpyHostToDevice));
+  std::vector<double> ref, got((size_t)count);
+  // the sample as a burst, once to warm up and once timed: queries/s; the
+  // estimates must equal those of the first case timed, bit for bit
+  auto burst = [&](double* qps) -> pw_status {
     double secs = 0.0;
-    for (int rep = 0; rep < 2; ++rep) {  // a warm-up burst, then the timed one
+    for (int rep = 0; rep < 2; ++rep) {
       const double t0 = now_ms();
       for (int64_t i = 0; i < count; ++i) {
         const pw_status st = pw_server_submit(sv, s[i], t[i], eps[i], L[i], seeds ? seeds + i : nullptr, &tk[(size_t)i]);
@@ -770,12 +776,61 @@ pw_status pw_server_tune(pw_server* sv, int64_t count, const int64_t* s, const i
       if (st != PW_OK) return st;
       secs = (now_ms() - t0) / 1000.0;
       for (int64_t i = 0; i < count; ++i) {
-        double b;
-        st = pw_server_poll(sv, tk[(size_t)i], &b);
+        st = pw_server_poll(sv, tk[(size_t)i], &got[(size_t)i]);
         if (st != PW_OK) return set_error(st, "pw_server_tune: a sample query failed");
       }
     }
-    out->queries_per_s[c] = (double)count / secs;
+    if (ref.empty()) ref = got;
+    if (memcmp(ref.data(), got.data(), sizeof(double) * (size_t)count) != 0)
+      return set_error(PW_ERR_INTERNAL, "pw_server_tune: two server variants gave different estimates");
+    *qps = (double)count / secs;
+    return PW_OK;
+  };
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  if (!table) {
+    // Without a table every policy runs the same per-visit jobs; what can be
+    // chosen is the kernel's occupancy.  The running kernel (idle, about to
+    // exit) finishes before the variant changes, so each burst is served by
+    // the variant it times.
+    int best = 0;
+    for (int v = 0; v < 2; ++v) {
+      PW_CUDA_TRY(cudaStreamSynchronize(sv->kstream));
+      {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->minb = 2 + v;
+        sv->grid = sv->grids[v];
+      }
+      const pw_status st = burst(&out->occupancy_qps[v]);
+      if (st != PW_OK) return st;
+      if (out->occupancy_qps[v] > out->occupancy_qps[best]) best = v;
+    }
+    PW_CUDA_TRY(cudaStreamSynchronize(sv->kstream));
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->minb = 2 + best;
+      sv->grid = sv->grids[best];
+    }
+    out->queries_per_s[0] = out->occupancy_qps[best];
+    out->policy = 0;
+    out->occupancy = 2 + best;
+    return PW_OK;
+  }
+  // candidate policies {table cost per probe, saving per visit}: the default
+  // model, the graph's batch-fitted model, every query per-visit, every query
+  // on the table
+  const double cand[4][2] = {{(double)g->n, 2.5}, {g->table_probe_cost, g->table_visit_gain}, {1.0, 0.0}, {0.0, 1.0}};
+  const bool valid[4] = {true, g->tuned != 0, true, true};
+  int best = 0;
+  for (int c = 0; c < 4; ++c) {
+    if (!valid[c]) continue;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->table_probe_cost = cand[c][0];
+      sv->table_visit_gain = cand[c][1];
+    }
+    PW_CUDA_TRY(cudaMemcpy(sv->d_model, cand[c], 2 * sizeof(double), cudaMemcpyHostToDevice));
+    const pw_status st = burst(&out->queries_per_s[c]);
+    if (st != PW_OK) return st;
     if (out->queries_per_s[c] > out->queries_per_s[best]) best = c;
   }
   {
@@ -785,6 +840,7 @@ pw_status pw_server_tune(pw_server* sv, int64_t count, const int64_t* s, const i
   }
   PW_CUDA_TRY(cudaMemcpy(sv->d_model, cand[best], 2 * sizeof(double), cudaMemcpyHostToDevice));
   out->policy = best;
+  out->occupancy = 4;
   return PW_OK;
 }
 

@@ -20,14 +20,15 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libprobewalk.so")
 
 PW_OK, PW_PENDING = 0, 1
 PW_ERR_ARG, PW_ERR_GRAPH, PW_ERR_NOMEM, PW_ERR_CUDA = -1, -2, -3, -4
-PW_ERR_TIMEOUT, PW_ERR_CANCELLED, PW_ERR_FULL = -5, -6, -7
+PW_ERR_TIMEOUT, PW_ERR_CANCELLED, PW_ERR_FULL, PW_ERR_INTERNAL = -5, -6, -7, -8
 PW_BUDGET_PILOT, PW_BUDGET_THEORY, PW_BUDGET_SCALED, PW_BUDGET_FIXED, PW_BUDGET_ADAPTIVE = 0, 1, 2, 3, 4
 TAG_WALK, TAG_WALK_PILOT, TAG_PROBE, TAG_PROBE_PILOT = 1, 2, 3, 4
 # pw_graph_load flags: skip the connectivity check; force the fused or the split walk layout
 LOAD_NO_CONNECTIVITY, LOAD_FUSED, LOAD_SPLIT = 1, 2, 4
 
 _STATUS_NAMES = {0: "PW_OK", 1: "PW_PENDING", -1: "PW_ERR_ARG", -2: "PW_ERR_GRAPH", -3: "PW_ERR_NOMEM",
-                 -4: "PW_ERR_CUDA", -5: "PW_ERR_TIMEOUT", -6: "PW_ERR_CANCELLED", -7: "PW_ERR_FULL"}
+                 -4: "PW_ERR_CUDA", -5: "PW_ERR_TIMEOUT", -6: "PW_ERR_CANCELLED", -7: "PW_ERR_FULL",
+                 -8: "PW_ERR_INTERNAL"}
 
 
 class PWError(RuntimeError):
@@ -65,7 +66,8 @@ def make_params(**kw) -> pw_params:
 
 
 class pw_server_tune_result(ctypes.Structure):
-    _fields_ = [("queries_per_s", ctypes.c_double * 4), ("policy", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+    _fields_ = [("queries_per_s", ctypes.c_double * 4), ("occupancy_qps", ctypes.c_double * 2),
+                ("policy", ctypes.c_int32), ("occupancy", ctypes.c_int32)]
 
 
 class pw_profile_stats(ctypes.Structure):
@@ -374,7 +376,8 @@ def pw_server_drain(srv: int, timeout_ms: int = 60000) -> None:
 
 
 def pw_server_tune(srv: int, s, t, eps, L, seeds=None) -> dict:
-    """Time the sample through the server under each walk-kernel policy and keep the fastest."""
+    """Time the sample through the server under each walk-kernel policy (or, when the
+    probe table does not fit, at each occupancy of the per-visit kernel) and keep the fastest."""
     s = _arr(s, np.int64)
     n = s.size
     t = _arr(t, np.int64)
@@ -384,7 +387,8 @@ def pw_server_tune(srv: int, s, t, eps, L, seeds=None) -> dict:
     out = pw_server_tune_result()
     _check(lib().pw_server_tune(srv, n, _p(s, _i64), _p(t, _i64), _p(eps, _dbl), _p(L, _i32),
                                 None if sd is None else _p(sd, _u64), ctypes.byref(out)))
-    return {"queries_per_s": list(out.queries_per_s), "policy": out.policy}
+    return {"queries_per_s": list(out.queries_per_s), "occupancy_qps": list(out.occupancy_qps),
+            "policy": out.policy, "occupancy": out.occupancy}
 
 
 def pw_server_destroy(srv: int) -> None:

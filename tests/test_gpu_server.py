@@ -8,7 +8,7 @@ import time
 import numpy as np
 import pytest
 
-from pw_inputs import barabasi_albert, eps_uniform, query_seeds, uniform_pairs
+from pw_inputs import barabasi_albert, eps_uniform, grid_deleted, query_seeds, uniform_pairs
 
 pytestmark = pytest.mark.gpu
 
@@ -248,8 +248,9 @@ def test_server_tune_keeps_results(pw):
         srv = pw.pw_server_create(g.handle, None, 1 << 26)
         try:
             r = pw.pw_server_tune(srv, s[:6], t[:6], 0.2, 40, seeds[:6])
-            assert r["policy"] in (0, 1, 2, 3)
+            assert r["policy"] in (0, 1, 2, 3) and r["occupancy"] == 4
             assert all(r["queries_per_s"][p] > 0 for p in (0, 1, 2, 3))
+            assert r["occupancy_qps"] == [0.0, 0.0]
             assert r["queries_per_s"][r["policy"]] == max(r["queries_per_s"])
             tk = [pw.pw_server_submit(srv, int(s[i]), int(t[i]), 0.2, 40, int(seeds[i])) for i in range(12)]
             pw.pw_server_drain(srv, 60000)
@@ -257,3 +258,32 @@ def test_server_tune_keeps_results(pw):
         finally:
             pw.pw_server_destroy(srv)
         np.testing.assert_array_equal(got, want)
+
+
+def test_server_tune_occupancy_without_table(pw):
+    """On a graph whose probe table does not fit in shared memory (n above
+    1,638,336) every policy runs the same per-visit jobs, so pw_server_tune times
+    the server kernel at 2 and at 3 blocks/SM and keeps the faster.  The tuner
+    requires both variants to give the same estimates bit for bit, and the
+    server's estimates after tuning equal the batch entry point's."""
+    h = grid_deleted(1400, 0.05, 7)
+    assert h.n > 1_638_336
+    with pw.Graph(h.row_ptr, h.col_idx) as g:
+        s, t = uniform_pairs(h.n, 8, 970)
+        seeds = query_seeds(8, 971)
+        want, st = pw.pw_query_batch(g.handle, s, t, 0.2, 60, seeds)
+        assert np.all(st == 0)
+        srv = pw.pw_server_create(g.handle, None, 1 << 26)
+        try:
+            r = pw.pw_server_tune(srv, s[:4], t[:4], 0.2, 60, seeds[:4])
+            assert r["policy"] == 0 and r["occupancy"] in (2, 3)
+            assert all(q > 0 for q in r["occupancy_qps"])
+            assert r["queries_per_s"][0] == max(r["occupancy_qps"])
+            assert r["queries_per_s"][1:] == [0.0, 0.0, 0.0]
+            tk = [pw.pw_server_submit(srv, int(s[i]), int(t[i]), 0.2, 60, int(seeds[i])) for i in range(8)]
+            pw.pw_server_drain(srv, 120000)
+            got = [pw.pw_server_poll(srv, x)[1] for x in tk]
+        finally:
+            pw.pw_server_destroy(srv)
+        np.testing.assert_array_equal(got, want)
+
