@@ -310,7 +310,7 @@ def run_serving(args, wl, world, rank, local):
     L = wl["L"]
     g = pw.Graph(host.row_ptr, host.col_idx, device=local)
     if not args.no_autotune:
-        k = min(n, 8)
+        k = min(n, args.tune_sample)
         pw.pw_autotune(g.handle, s[:k], t[:k], eps[:k], np.full(k, L, np.int32), seeds[:k])
     srv = pw.pw_server_create(g.handle, None, 8 << 30)
     out = {}
@@ -388,7 +388,7 @@ def run_scale_batch(args, wl, world, rank, local):
     params = pw.make_params(c_B=args.c_B)
     tune = None
     if not args.no_autotune:
-        k = min(n, 8)
+        k = min(n, args.tune_sample)
         tune = pw.pw_autotune(g.handle, s[:k], t[:k], eps[:k], L[:k], seeds[:k], params)
     d = [torch.from_numpy(a).to(dev) for a in (s, t, eps, L, seeds.view(np.int64))]
     beta = torch.empty(n, dtype=torch.float64, device=dev)
@@ -707,9 +707,12 @@ def run_ours(args, wl, world, rank, local):
     # walk-kernel cost model fitted on this graph (outside every timed region)
     tune = None
     if args.walk_mode == 0 and not args.no_autotune:
-        k = min(nq, 8)
+        k = min(nq, args.tune_sample)
         tune = pw.pw_autotune(g.handle, s[:k], t[:k], eps[:k], L[:k], seeds[:k], params)
         tune["sample"] = f"first {k} queries of the batch"
+    if args.l2_window >= 0:
+        pw.pw_graph_set_l2_window(g.handle, args.l2_window)
+    l2_window = args.l2_window if args.l2_window >= 0 else (tune["l2_window"] if tune else 0)
 
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
@@ -867,6 +870,8 @@ def run_ours(args, wl, world, rank, local):
             "walk_kernel": {1: "per-visit probe evaluation", 2: "per-probe shared-memory table",
                             3: "both (chosen per query)"}.get(walk_mode, "?"),
             "autotune": tune,
+            "l2_window": {0: "none", 1: "gathered array (persisting share = set-aside / array)",
+                          2: "node records"}[l2_window],
             "transitions_per_step": transitions_per_step,
             "plain_queries_per_s": plain_qps, "plain_sample": plain_n,
             "batched_over_plain": (value / world) / plain_qps if plain_qps else None,
@@ -905,6 +910,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-server", action="store_true")
     ap.add_argument("--no-tiny", action="store_true", help="skip the tiny-graph batched-vs-plain comparison")
+    ap.add_argument("--tune-sample", type=int, default=32,
+                    help="queries of the pw_autotune sample (the first ones of the batch)")
+    ap.add_argument("--l2-window", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="L2 access-policy window of the walks: -1 the autotuner's choice, 0 none, "
+                         "1 the gathered array, 2 node records (split layout)")
     ap.add_argument("--layout", type=int, default=0, choices=[0, 1, 2],
                     help="walk layout: 0 by size, 1 fused records, 2 col_idx + node records")
     ap.add_argument("--stabilized", action="store_true", help="L by the stabilization rule (Section 4.3)")

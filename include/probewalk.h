@@ -120,6 +120,24 @@ pw_status pw_graph_load32(int32_t n, const int32_t* row_ptr, const int32_t* col_
 /* Releases the device copy and scratch of a loaded graph (NULL is a no-op).
  * No call on g may be in flight; servers on g must be destroyed first. */
 void pw_graph_free(pw_graph* g);
+/* L2 access-policy window of the walk launches on g (an implementation choice:
+ * the paper says nothing about caching; estimates do not depend on it).
+ * which: 0 none (the default); 1 the array every walk step gathers from (the
+ * fused records, or col_idx on the split layout), uniformly at stationarity;
+ * 2 the split layout's node records, gathered in proportion to degree, so
+ * hub nodes' records most often.  The window covers the array, up to the
+ * device's maximum window size; the context's persisting-L2 set-aside is
+ * raised to min(device maximum, window bytes), and the window's hit ratio is
+ * set-aside / window bytes, so that the lines marked persisting fit; the
+ * others are streaming.  Every later walk-kernel and server launch on g
+ * carries the window as a launch attribute (the caller's streams are not
+ * modified).  which = 0 returns the persisting lines to normal and the
+ * set-aside to its value before; pw_graph_free does the same.  Call it with
+ * no call on g in flight and no server on g.  PW_ERR_ARG for which outside
+ * {0, 1, 2} or 2 on the fused layout; PW_ERR_CUDA when the device has no
+ * persisting L2 or the set-aside cannot be set.  pw_autotune times the
+ * windows and keeps the fastest. */
+pw_status pw_graph_set_l2_window(pw_graph* g, int32_t which);
 /* Graph facts: n, nnz (directed entries), minimum and maximum degree,
  * bipartite flag (1 when 2-colourable: the paper assumes non-bipartite,
  * Section 2.1; estimates then target beta^(L) only).  Any output may be NULL. */
@@ -402,7 +420,11 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
  * pw_server_tune).  Costs are whole-GPU nanoseconds.  When the graph's table
  * does not fit in shared memory (one bit per node in at most 200 KB:
  * n > 1,638,336) only the per-visit runs are made and table_available = 0;
- * the model then always picks per-visit.  params as in
+ * the model then always picks per-visit.  Finally the sample runs at the
+ * caller's budget under each L2 window of pw_graph_set_l2_window (none, the
+ * gathered array, and on the split layout the node records; the windows the
+ * device cannot set are skipped); the fastest window is kept if it beats no
+ * window by 2 % or more, else none.  params as in
  * pw_query (its walk_mode is ignored).  Errors as pw_query_batch; the
  * estimates of the runs are discarded. */
 typedef struct pw_tune_result {
@@ -416,7 +438,8 @@ typedef struct pw_tune_result {
   int32_t table_threads;   /* table-kernel block size kept: 256, 512 or 1024 (0 when unavailable) */
   double policy_ms[3];     /* walk time of the sample at the caller's budget: per-query model, all per-visit, all table */
   int32_t policy;          /* the policy walk_mode 0 now follows: 0 per-query model, 1 all per-visit, 2 all table */
-  int32_t reserved;
+  int32_t l2_window;       /* the L2 window kept (pw_graph_set_l2_window): 0 none, 1 gathered array, 2 node records */
+  double window_ms[3];     /* walk time of the sample at the caller's budget under window 0, 1, 2 (0: not timed) */
 } pw_tune_result;
 pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_t* t, const double* eps,
                       const int32_t* L, const uint64_t* seeds, const pw_params* params, pw_tune_result* out);

@@ -188,10 +188,59 @@ static pw_status upload(pw_graph* g, const int64_t* rp64, const int32_t* col) {
   return PW_OK;
 }
 
+// The L2 access-policy window of the walk launches (see pw_graph_set_l2_window).
+// Caller holds g->lock or owns g alone.
+pw_status set_l2_window(pw_graph* g, int which) {
+  PW_CUDA_TRY(cudaSetDevice(g->device));
+  if (g->l2_window) cudaCtxResetPersistingL2Cache();  // the old window's lines become normal
+  g->l2_window = 0;
+  g->l2_apw = cudaAccessPolicyWindow{};
+  if (which == 0) {
+    if (g->l2_limit_set) {
+      g->l2_limit_set = false;
+      PW_CUDA_TRY(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g->l2_prev_limit));
+    }
+    return PW_OK;
+  }
+  int max_persist = 0, max_window = 0;
+  PW_CUDA_TRY(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, g->device));
+  PW_CUDA_TRY(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, g->device));
+  if (max_persist <= 0 || max_window <= 0) return set_error(PW_ERR_CUDA, "the device has no persisting L2");
+  void* base = nullptr;
+  size_t bytes = 0;
+  if (which == 1 && g->layout == 2) {
+    base = g->d_col;
+    bytes = sizeof(int32_t) * (size_t)g->nnz;
+  } else if (which == 1) {
+    base = g->d_rec;
+    bytes = sizeof(int4) * (size_t)g->nnz;
+  } else {
+    base = g->d_node;
+    bytes = sizeof(int4) * (size_t)g->n;
+  }
+  const size_t num = bytes < (size_t)max_window ? bytes : (size_t)max_window;
+  const size_t want = num < (size_t)max_persist ? num : (size_t)max_persist;
+  if (!g->l2_limit_set) PW_CUDA_TRY(cudaDeviceGetLimit(&g->l2_prev_limit, cudaLimitPersistingL2CacheSize));
+  PW_CUDA_TRY(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+  g->l2_limit_set = true;
+  size_t got = 0;
+  PW_CUDA_TRY(cudaDeviceGetLimit(&got, cudaLimitPersistingL2CacheSize));  // as granted
+  if (got == 0) return set_error(PW_ERR_CUDA, "no persisting L2 set-aside granted");
+  // a hit ratio that fits the window's persisting lines in the set-aside
+  g->l2_apw.base_ptr = base;
+  g->l2_apw.num_bytes = num;
+  g->l2_apw.hitRatio = got >= num ? 1.0f : (float)((double)got / (double)num);
+  g->l2_apw.hitProp = cudaAccessPropertyPersisting;
+  g->l2_apw.missProp = cudaAccessPropertyStreaming;
+  g->l2_window = which;
+  return PW_OK;
+}
+
 static void destroy(pw_graph* g) {
   if (!g) return;
   cudaSetDevice(g->device);
   if (g->stream) cudaStreamSynchronize(g->stream);
+  if (g->l2_window || g->l2_limit_set) set_l2_window(g, 0);
   free_workspace(g->ws);
   for (auto& sp : g->prof.spans) {
     cudaEventDestroy(sp.a);
@@ -266,6 +315,14 @@ pw_status pw_graph_load32(int32_t n, const int32_t* row_ptr, const int32_t* col_
 }
 
 void pw_graph_free(pw_graph* g) { pw::destroy(g); }
+
+pw_status pw_graph_set_l2_window(pw_graph* g, int32_t which) {
+  if (!g) return pw::set_error(PW_ERR_ARG, "graph is NULL");
+  if (which < 0 || which > 2) return pw::set_error(PW_ERR_ARG, "which must be 0, 1 or 2");
+  if (which == 2 && g->layout != 2) return pw::set_error(PW_ERR_ARG, "a node-record window needs the split layout");
+  std::lock_guard<std::mutex> guard(g->lock);
+  return pw::set_l2_window(g, which);
+}
 
 pw_status pw_graph_info(const pw_graph* g, int64_t* n, int64_t* nnz, int32_t* d_min, int32_t* d_max,
                         int32_t* bipartite) {

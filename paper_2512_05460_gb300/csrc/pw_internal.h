@@ -121,6 +121,14 @@ struct pw_graph {
   int visit_minb = 1;
   int table_threads = 0;
   int walk_policy = 0;  // walk_mode 0 means: 0 the cost model per query, 1 all per-visit, 2 all table
+  // L2 access-policy window of the walk and server launches
+  // (pw_graph_set_l2_window): 0 none, 1 the uniformly gathered array, 2 the
+  // node records.  l2_prev_limit: the context's persisting set-aside before
+  // this graph raised it (restored when the window is dropped).
+  int l2_window = 0;
+  cudaAccessPolicyWindow l2_apw{};
+  size_t l2_prev_limit = 0;
+  bool l2_limit_set = false;
   std::mutex lock;
   pw::GraphCache gcache;
   pw::Workspace ws;
@@ -129,7 +137,32 @@ struct pw_graph {
 
 namespace pw {
 
+// Launches fn on the graph's walk data: with the graph's L2 access-policy
+// window as a launch attribute when one is set (the stream's own attributes
+// are left alone), else a plain launch.
+template <class... K, class... A>
+inline cudaError_t launch_with_window(const pw_graph* g, void (*fn)(K...), int grid, int threads, size_t smem,
+                                      cudaStream_t stream, A&&... args) {
+  if (!g->l2_window) {
+    fn<<<grid, threads, smem, stream>>>(args...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+  attr[0].val.accessPolicyWindow = g->l2_apw;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, static_cast<A&&>(args)...);
+}
+
 pw_status set_error(pw_status st, const std::string& msg);
+// pw_graph_set_l2_window without the argument checks and the lock.
+pw_status set_l2_window(pw_graph* g, int which);
 // CUDA-event spans on a graph's stream, summed by pw_profile (no-ops unless enabled).
 void prof_begin(pw_graph* g, cudaStream_t stream, cudaEvent_t* a);
 void prof_end(pw_graph* g, cudaStream_t stream, cudaEvent_t a, int kind);

@@ -535,9 +535,9 @@ static int grid_of(pw_graph* g, WalkFn fn, int threads, size_t smem) {
 
 static pw_status launch_walk(pw_graph* g, cudaStream_t stream, const WalkArgs& a, bool debug, bool pilot) {
   const WalkFn fn = walk_fn(debug, pilot, g->layout == 2, g->visit_minb);
-  fn<<<grid_of(g, fn, kWalkThreads, 0), kWalkThreads, 0, stream>>>(a);
+  const cudaError_t e = launch_with_window(g, fn, grid_of(g, fn, kWalkThreads, 0), kWalkThreads, 0, stream, a);
   count_launch();
-  PW_CUDA_TRY(cudaGetLastError());
+  PW_CUDA_TRY(e);
   return PW_OK;
 }
 
@@ -549,9 +549,9 @@ static pw_status launch_table(pw_graph* g, cudaStream_t stream, const WalkArgs& 
   const size_t smem = table_bytes(g);
   const int threads = debug ? 256 : table_threads(g);
   const WalkFn fn = table_fn(debug, g->layout == 2, threads);
-  fn<<<grid_of(g, fn, threads, smem), threads, smem, stream>>>(a);
+  const cudaError_t e = launch_with_window(g, fn, grid_of(g, fn, threads, smem), threads, smem, stream, a);
   count_launch();
-  PW_CUDA_TRY(cudaGetLastError());
+  PW_CUDA_TRY(e);
   return PW_OK;
 }
 
@@ -884,6 +884,7 @@ static pw_status graph_batch(pw_graph* g, int64_t count, const char* h, char* ho
   key_put(key, g->visit_minb);
   key_put(key, g->walk_policy);
   key_put(key, g->table_threads);
+  key_put(key, g->l2_window);
   key_put(key, B);
   key_put(key, ws.queries.ptr);
   key_put(key, ws.results.ptr);
@@ -1317,6 +1318,7 @@ pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_
   else
     memset(&p, 0, sizeof p);
   const pw_params caller = p;
+  if ((st = set_l2_window(g, 0)) != PW_OK) return st;  // variants are timed without a window
   p.budget_mode = PW_BUDGET_FIXED;
   p.B = 16;
   p.G = ba.G;
@@ -1362,10 +1364,36 @@ pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_
   out->sample_ms[0] = dv.d.walk_ms;
   out->visit_ns = dv.n_visits > 0 ? 1e6 * dv.d.walk_ms / dv.n_visits : 0.0;
   out->sample_mode = 1;
+  // L2 windows, timed on the caller's budget with everything else as kept
+  auto tune_window = [&]() -> pw_status {
+    p = caller;
+    p.walk_mode = 0;
+    int best_w = 0;
+    for (int w = 0; w < 3; ++w) {
+      if (w == 2 && g->layout != 2) continue;
+      if (set_l2_window(g, w) != PW_OK) continue;  // not available on this device
+      DebugOut d;
+      for (int rep = 0; rep < 2; ++rep) {
+        d = DebugOut();
+        d.time_walk = true;
+        const pw_status st2 = host_batch(g, count, s, t, eps, L, seeds, &p, beta.data(), status.data(), &d);
+        if (st2 != PW_OK) {
+          set_l2_window(g, 0);
+          return st2;
+        }
+      }
+      out->window_ms[w] = d.walk_ms;
+      // a window takes persisting L2 from the whole context: kept only when
+      // it beats no window by 2 % or more
+      if (w > 0 && d.walk_ms < 0.98 * out->window_ms[0] && d.walk_ms < out->window_ms[best_w]) best_w = w;
+    }
+    out->l2_window = best_w;
+    return set_l2_window(g, best_w);
+  };
   if (table_bytes(g) > kMaxTableBytes) {
     g->table_visit_gain = 0.0;  // the table cannot be built: always per-visit
     g->tuned = 1;
-    return PW_OK;
+    return tune_window();
   }
   out->table_available = 1;
   // table kernel: block size
@@ -1432,7 +1460,7 @@ pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_
   }
   g->walk_policy = best_policy;
   out->policy = best_policy;
-  return PW_OK;
+  return tune_window();
 }
 
 pw_status pw_debug_exact_sum(pw_graph* g, const float* u, int64_t n, double* S1, double* S2) {

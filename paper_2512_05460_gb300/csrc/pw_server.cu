@@ -577,9 +577,8 @@ static void worker_loop(pw_server* sv) {
         cudaEventDestroy(ev);
         cudaMemsetAsync(sv->d_ctl + 4, 0, sizeof(unsigned long long), sv->kstream);  // exit flag
         const ServerFn fn = server_fn(args.table_words > 0, sv->g->layout, minb);
-        fn<<<grid, kServerThreads, sv->smem, sv->kstream>>>(args);
+        const cudaError_t e = launch_with_window(sv->g, fn, grid, kServerThreads, sv->smem, sv->kstream, args);
         count_launch();
-        const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
           std::lock_guard<std::mutex> lk(sv->mu);
           sv->fatal = cuda_error(e, "server_kernel launch");

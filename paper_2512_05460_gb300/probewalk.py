@@ -98,7 +98,8 @@ class pw_tune_result(ctypes.Structure):
         ("table_threads", ctypes.c_int32),
         ("policy_ms", ctypes.c_double * 3),
         ("policy", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("l2_window", ctypes.c_int32),
+        ("window_ms", ctypes.c_double * 3),
     ]
 
 
@@ -114,6 +115,7 @@ SIGNATURES = {
     "pw_graph_load": (_i32, [_i64, P(_i64), P(_i32), _i64, _i32, _u32, P(_vp)]),
     "pw_graph_load32": (_i32, [_i32, P(_i32), P(_i32), _i32, _i32, _u32, P(_vp)]),
     "pw_graph_free": (None, [_vp]),
+    "pw_graph_set_l2_window": (_i32, [_vp, _i32]),
     "pw_graph_info": (_i32, [_vp, P(_i64), P(_i64), P(_i32), P(_i32), P(_i32)]),
     "pw_budget": (_i32, [_vp, _i64, _i64, _dbl, _i32, P(_u64), P(pw_params), P(_u64), P(_u64), P(_u64), P(_u64)]),
     "pw_default_seed": (_u64, [_u64, _i64, _i64, _dbl, _i32]),
@@ -218,6 +220,11 @@ def pw_graph_load32(row_ptr, col_idx, device: int = 0, flags: int = 0) -> int:
 
 def pw_graph_free(g: int) -> None:
     lib().pw_graph_free(g)
+
+
+def pw_graph_set_l2_window(g: int, which: int) -> None:
+    """L2 access-policy window of the walk launches: 0 none, 1 the gathered array, 2 the node records."""
+    _check(lib().pw_graph_set_l2_window(g, int(which)))
 
 
 def pw_graph_info(g: int) -> dict:
@@ -491,7 +498,8 @@ def pw_autotune(g: int, s, t, eps, L, seeds=None, params=None) -> dict:
     return {"visit_ns": out.visit_ns, "table_visit_ns": out.table_visit_ns, "table_probe_ns": out.table_probe_ns,
             "sample_ms": list(out.sample_ms), "table_available": out.table_available,
             "sample_mode": out.sample_mode, "visit_occupancy": out.visit_occupancy,
-            "table_threads": out.table_threads, "policy_ms": list(out.policy_ms), "policy": out.policy}
+            "table_threads": out.table_threads, "policy_ms": list(out.policy_ms), "policy": out.policy,
+            "l2_window": out.l2_window, "window_ms": list(out.window_ms)}
 
 
 def pw_profile(g: int, enable: bool = True, reset: bool = False) -> dict:

@@ -54,6 +54,12 @@ def test_autotune_fits_and_auto_mode_follows_it(pw):
     assert r["policy_ms"][r["policy"]] == min(r["policy_ms"])
     if r["policy"] != 0:
         want_mode = r["policy"]
+    # L2 window: none and the gathered records timed (fused layout: no node-record window)
+    timed = [x for x in r["window_ms"] if x > 0]
+    assert r["window_ms"][0] > 0 and r["window_ms"][2] == 0
+    assert r["l2_window"] in (0, 1)
+    if r["l2_window"]:
+        assert r["window_ms"][r["l2_window"]] == min(timed) < 0.98 * r["window_ms"][0]
     pw.pw_profile(g.handle, enable=True, reset=True)
     b0, m0 = _batch(pw, g, s, t, eps, L, seeds, 0)
     assert m0 == want_mode
@@ -81,6 +87,10 @@ def test_autotune_without_table(pw):
     r = pw.pw_autotune(g.handle, s, t, 0.2, 20, seeds)
     assert r["table_available"] == 0 and r["sample_mode"] == 1
     assert r["visit_ns"] > 0 and r["table_probe_ns"] == 0 and r["table_visit_ns"] == 0
+    timed = [x for x in r["window_ms"] if x > 0]
+    assert r["window_ms"][0] > 0 and r["l2_window"] in (0, 1, 2)
+    if r["l2_window"]:
+        assert r["window_ms"][r["l2_window"]] == min(timed) < 0.98 * r["window_ms"][0]
     pw.pw_profile(g.handle, enable=True, reset=True)
     b0, m0 = _batch(pw, g, s, t, 0.2, 20, seeds, 0)
     assert m0 == 1
@@ -97,3 +107,43 @@ def test_autotune_rejects_bad_sample(pw):
     with pytest.raises(pw.PWError):
         pw.pw_autotune(g.handle, [0], [h.n + 5], 0.1, 10)
     g.close()
+
+
+@pytest.mark.parametrize("layout", ["fused", "split"])
+def test_l2_window_keeps_estimates(pw, layout):
+    """An L2 access-policy window changes only what stays in L2: with each
+    window the batch (eager, captured, replayed) and the server give the
+    estimates of the launches without one; on the fused layout the
+    node-record window is rejected."""
+    h = barabasi_albert(20_000, 5, 31)
+    flags = pw.LOAD_FUSED if layout == "fused" else pw.LOAD_SPLIT
+    g = pw.Graph(h.row_ptr, h.col_idx, flags=flags)
+    s, t = uniform_pairs(h.n, 6, 990)
+    seeds = query_seeds(6, 991)
+    want, st = pw.pw_query_batch(g.handle, s, t, 0.2, 40, seeds)
+    assert np.all(st == 0)
+    windows = (1,) if layout == "fused" else (1, 2)
+    if layout == "fused":
+        with pytest.raises(pw.PWError):
+            pw.pw_graph_set_l2_window(g.handle, 2)
+    with pytest.raises(pw.PWError):
+        pw.pw_graph_set_l2_window(g.handle, 3)
+    for w in windows:
+        pw.pw_graph_set_l2_window(g.handle, w)
+        for _ in range(3):  # eager, then captured into a CUDA graph, then replayed
+            got, st = pw.pw_query_batch(g.handle, s, t, 0.2, 40, seeds)
+            assert np.all(st == 0)
+            np.testing.assert_array_equal(got, want)
+        srv = pw.pw_server_create(g.handle, None, 1 << 26)
+        try:
+            tk = [pw.pw_server_submit(srv, int(s[i]), int(t[i]), 0.2, 40, int(seeds[i])) for i in range(6)]
+            pw.pw_server_drain(srv, 60000)
+            got = [pw.pw_server_poll(srv, x)[1] for x in tk]
+        finally:
+            pw.pw_server_destroy(srv)
+        np.testing.assert_array_equal(got, want)
+    pw.pw_graph_set_l2_window(g.handle, 0)
+    got, _ = pw.pw_query_batch(g.handle, s, t, 0.2, 40, seeds)
+    np.testing.assert_array_equal(got, want)
+    g.close()
+
