@@ -309,11 +309,11 @@ def run_serving(args, wl, world, rank, local):
     eps = workload_eps(wl, n, rank)
     L = wl["L"]
     g = pw.Graph(host.row_ptr, host.col_idx, device=local)
+    out = {}
     if not args.no_autotune:
         k = min(n, args.tune_sample)
-        pw.pw_autotune(g.handle, s[:k], t[:k], eps[:k], np.full(k, L, np.int32), seeds[:k])
+        out["graph_tune"] = pw.pw_autotune(g.handle, s[:k], t[:k], eps[:k], np.full(k, L, np.int32), seeds[:k])
     srv = pw.pw_server_create(g.handle, None, 8 << 30)
-    out = {}
     try:
         k = min(n, 32)
         out["tune"] = pw.pw_server_tune(srv, s[:k], t[:k], eps[:k], np.full(k, L, np.int32), seeds[:k])
