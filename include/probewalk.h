@@ -415,8 +415,9 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
  * probes * table_probe_ns < visits * (visit_ns - table_visit_ns).  Last,
  * the sample runs once more at the caller's own budget under three policies
  * (that model per query, every query per-visit, every query on the table),
- * and walk_mode 0 follows the fastest from then on (with the table
- * unavailable, policy 0 and 1 coincide).  Servers keep their own policy (see
+ * and walk_mode 0 follows the fastest from then on; a single-kernel policy
+ * within 1 % of the model is preferred to it (one walk launch per batch
+ * instead of two).  With the table unavailable, policy 0 and 1 coincide.  Servers keep their own policy (see
  * pw_server_tune).  Costs are whole-GPU nanoseconds.  When the graph's table
  * does not fit in shared memory (one bit per node in at most 200 KB:
  * n > 1,638,336) only the per-visit runs are made and table_available = 0;

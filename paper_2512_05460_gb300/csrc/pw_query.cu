@@ -1458,6 +1458,12 @@ pw_status pw_autotune(pw_graph* g, int64_t count, const int64_t* s, const int64_
       best_policy = policy;
     }
   }
+  // A model that mixes the kernels runs two walk launches per batch, each
+  // with its own tail; a single-kernel policy within 1 % of it is kept instead.
+  if (best_policy == 0) {
+    const int single = out->policy_ms[1] <= out->policy_ms[2] ? 1 : 2;
+    if (out->policy_ms[single] <= 1.01 * out->policy_ms[0]) best_policy = single;
+  }
   g->walk_policy = best_policy;
   out->policy = best_policy;
   return tune_window();

@@ -51,7 +51,11 @@ def test_autotune_fits_and_auto_mode_follows_it(pw):
     want_mode = (1 if not all(table) else 0) | (2 if any(table) else 0)
     # ... unless the timed policy check kept "all per-visit" or "all table"
     assert r["policy"] in (0, 1, 2) and all(x > 0 for x in r["policy_ms"])
-    assert r["policy_ms"][r["policy"]] == min(r["policy_ms"])
+    # the fastest, except that a single-kernel policy within 1 % of the model is preferred to it
+    if r["policy"] == 0:
+        assert r["policy_ms"][0] == min(r["policy_ms"]) and min(r["policy_ms"][1:]) > 1.01 * r["policy_ms"][0]
+    else:
+        assert r["policy_ms"][r["policy"]] <= 1.01 * min(r["policy_ms"])
     if r["policy"] != 0:
         want_mode = r["policy"]
     # L2 window: none and the gathered records timed (fused layout: no node-record window)
