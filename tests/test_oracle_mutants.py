@@ -45,6 +45,31 @@ MUTANTS = {
     "adaptive_biased_variance": ("double s2 = K1 > 1 ? ss / (double)(K1 - 1) : 0.0;", "double s2 = ss / (double)K1;"),
     # theta not floored by theta_0 (the floor from the proof of Theorem 3.8)
     "theta_unfloored": ("double theta = q_bar > theta0 ? q_bar : theta0;", "double theta = q_bar;"),
+    # zero set one element short (Definition 3.1: |U| = r)
+    "zero_set_off_by_one": ("if (pi >= P->n - P->r) return 0; /* i in U */",
+                            "if (pi > P->n - P->r) return 0; /* i in U */"),
+    # sign hash of the element instead of its pair (pairs must get opposite signs)
+    "hash_per_element": ("uint64_t pair = pi / 2;", "uint64_t pair = pi;"),
+    # walks one transition short (L transitions, L + 1 terms per side)
+    "one_step_short": ("  for (int32_t i = 1; i <= L; ++i) {\n    x = next_node(",
+                       "  for (int32_t i = 1; i < L; ++i) {\n    x = next_node("),
+    # the t-walk drawing the s-walk's random words (walks must be independent)
+    "t_walk_shares_stream": ("uint64_t wid_s = 2 * pair_index, wid_t = 2 * pair_index + 1;",
+                             "uint64_t wid_s = 2 * pair_index, wid_t = 2 * pair_index;"),
+    # pilot R from 2 sigma^2 / theta instead of Lemma 3.7's 4 sigma^2 / theta
+    "pilot_R_factor": ("double R = ceil_tol(c.c_R * 4.0 * sigma2 / theta);",
+                       "double R = ceil_tol(c.c_R * 2.0 * sigma2 / theta);"),
+    # G with log base 2 instead of the natural log (the proof needs exp(-G/8) <= delta)
+    "G_log2": ("uint64_t G = (uint64_t)ceil_tol(8.0 * log(1.0 / c.delta));",
+               "uint64_t G = (uint64_t)ceil_tol(8.0 * log2(1.0 / c.delta));"),
+    # plain ceiling: exact integers that evaluate a last place high round up
+    "ceil_no_tolerance": ("static double ceil_tol(double x) { return ceil(x * (1.0 - 1e-12)); }",
+                          "static double ceil_tol(double x) { return ceil(x); }"),
+    # strided blocks instead of contiguous ones (block g = probes [gB, (g+1)B))
+    "strided_blocks": ("for (uint64_t k = g * B; k < (g + 1) * B; ++k) sum = sum + q[k];",
+                       "for (uint64_t k = g; k < G * B; k += G) sum = sum + q[k];"),
+    # U-statistic without the square of S1 (Eq. Q-Ustat)
+    "s1_not_squared": ("return (S1 * S1 - S2) / (Rd * (Rd - 1.0));", "return (S1 - S2) / (Rd * (Rd - 1.0));"),
 }
 
 # Planted mistakes in a copy of oracle/exact.py, each caught by the closed forms
@@ -82,6 +107,9 @@ def _run_pins(g_tiny):
         ("L0_deterministic", lambda: walker_pins.test_L0_replicas_are_deterministic(None, g_tiny)),
         ("pilot_accuracy", lambda: walker_pins.test_pilot_accuracy_problem_1(None, g_tiny)),
         ("median_golden", lambda: walker_pins.test_median_of_means_golden(None)),
+        ("theory_budget_golden", lambda: walker_pins.test_theory_budget_golden(None)),
+        ("G_for_even_deltas", lambda: walker_pins.test_G_for_even_deltas(None, g_tiny)),
+        ("visits_are_walks", lambda: walker_pins.test_visits_are_the_walks_of_every_replica(None, g_tiny)),
         ("exact_sum_ties", lambda: walker_pins.test_exact_sum_ties_and_edges(None)),
         ("adaptive_golden", lambda: walker_pins.test_adaptive_rule_golden(None)),
         ("adaptive_rule", lambda: walker_pins.test_adaptive_budget_stopping_rule(None, g_tiny, 3, 77, 0.2, 32, 12345,

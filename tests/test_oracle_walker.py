@@ -142,9 +142,32 @@ def test_mean_of_estimates_is_unbiased(oracle_lib):
     assert abs(beta.mean() - want) < 5 * beta.std() / math.sqrt(beta.size)
 
 
+def test_visits_are_the_walks_of_every_replica(oracle_lib, tiny_graph):
+    """Replica p of probe k runs walk 2(kR + p) from s and walk 2(kR + p) + 1
+    from t (reading 8), each of L transitions with X_0 counted (L + 1 visits,
+    Algorithm 1's inner loop): the query's visit counts equal the histogram of
+    those trajectories drawn one by one."""
+    g = tiny_graph
+    s, t, L, seed = 3, 77, 7, 4242
+    B, G, R = 2, 3, 8
+    cfg = oracle.budget_cfg(mode=oracle.MODE_FIXED, B=B, G=G, R=R)
+    out = oracle.query(g, s, t, 0.2, L, seed, cfg, want_visits=True)
+    K = B * G
+    assert int(out["visits"].sum()) == 2 * K * R * (L + 1)
+    want = np.zeros(g.n, np.int64)
+    for k in range(K):
+        for p in range(R):
+            for side, start in ((0, s), (1, t)):
+                traj = oracle.walk(g, start, L, seed, 2 * (k * R + p) + side, oracle.TAG_WALK)
+                assert len(traj) == L + 1 and traj[0] == start
+                np.add.at(want, traj, 1)
+    np.testing.assert_array_equal(out["visits"].astype(np.int64), want)
+
+
 def test_theory_budget_golden(oracle_lib):
-    g = complete_graph(10)
     for row in _read_rows("budget_theory.txt"):
+        assert row[0].startswith("K")
+        g = complete_graph(int(row[0][1:]))
         eps, delta, L, s, t = float(row[1]), float(row[2]), int(row[3]), int(row[4]), int(row[5])
         B, G, K, R = (int(x) for x in row[6:10])
         got = oracle.budget(g, s, t, eps, L, 1, oracle.budget_cfg(mode=oracle.MODE_THEORY, delta=delta))
