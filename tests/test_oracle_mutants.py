@@ -70,6 +70,10 @@ MUTANTS = {
                        "for (uint64_t k = g; k < G * B; k += G) sum = sum + q[k];"),
     # U-statistic without the square of S1 (Eq. Q-Ustat)
     "s1_not_squared": ("return (S1 * S1 - S2) / (Rd * (Rd - 1.0));", "return (S1 - S2) / (Rd * (Rd - 1.0));"),
+    # parity coin stuck at r = 2 for even n (Definition 3.1 draws r in {0, 2})
+    "coin_always_two": ("P->r = 2u * (w[0] & 1u);", "P->r = 2u;"),
+    # a single Feistel pass, no cycle-walk back into [n]
+    "no_cycle_walk": ("  } while (x >= P->n);", "  } while (0);"),
 }
 
 # Planted mistakes in a copy of oracle/exact.py, each caught by the closed forms
@@ -102,6 +106,7 @@ def _run_pins(g_tiny):
     checks = [
         ("pairing_uniform_n7", lambda: probe_pins.test_pairing_is_uniform(None, 7)),
         ("probe_structure", lambda: probe_pins.test_probe_structure(None, 10)),
+        ("pi_permutation_odd_width", lambda: probe_pins.test_pi_is_permutation(None, 17)),
         ("neighbour_uniform", lambda: walker_pins.test_neighbour_sampling_uniform(None)),
         ("replicas_unbiased", lambda: walker_pins.test_replicas_unbiased_for_phi(None)),
         ("L0_deterministic", lambda: walker_pins.test_L0_replicas_are_deterministic(None, g_tiny)),
