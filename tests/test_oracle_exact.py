@@ -240,3 +240,61 @@ def test_effective_resistance_closed_forms():
 
 def test_mixing_lambda_closed_forms():
     check_mixing_lambda(exact)
+
+
+# ---------------------------------------------------------------------------
+# The same closed forms for beta, L^+ and the series, taking the module, so
+# that planted mistakes in a copy of it can be run through them.
+# ---------------------------------------------------------------------------
+
+
+def check_exact_beta(ex):
+    for n in (4, 7):  # K_n: 2/n^2 off the diagonal, 0 on it
+        g = complete_graph(n)
+        m = ex.exact_beta_matrix(g.row_ptr, g.col_idx, n)
+        np.testing.assert_allclose(m[~np.eye(n, dtype=bool)], 2.0 / n**2, rtol=1e-11)
+        np.testing.assert_allclose(np.diag(m), 0.0, atol=1e-12)
+    g = cycle_graph(9)  # C_9 closed form: 20/27, 56/27, 110/27
+    for delta, frac in ((1, 20 / 27), (2, 56 / 27), (4, 110 / 27)):
+        assert ex.exact_beta(g.row_ptr, g.col_idx, 9, 0, delta) == pytest.approx(frac, rel=1e-12)
+    g = path_graph(6)  # end to end of P_6: 35/2
+    assert ex.exact_beta(g.row_ptr, g.col_idx, 6, 0, 5) == pytest.approx(17.5, rel=1e-12)
+    g = er_cycle(40, 0.15, 2)  # Moore-Penrose conditions of L^+
+    lp = ex.laplacian_pinv(g.row_ptr, g.col_idx, g.n)
+    a = np.zeros((g.n, g.n))
+    a[np.repeat(np.arange(g.n), g.degrees), g.col_idx] = 1
+    lap = np.diag(a.sum(1)) - a
+    assert np.allclose(lap @ lp @ lap, lap, atol=1e-10)
+    assert np.allclose(lp @ lap @ lp, lp, atol=1e-10)
+    assert np.allclose(lp, lp.T, atol=1e-12)
+
+
+def check_series(ex):
+    for n, L in ((3, 0), (5, 1), (10, 5)):  # K_n: (2/n^2)(1 - (-1/(n-1))^(L+1))^2
+        g = complete_graph(n)
+        want = 2.0 / n**2 * (1 - (-1.0 / (n - 1)) ** (L + 1)) ** 2
+        assert ex.series_beta(g.row_ptr, g.col_idx, n, 0, n - 1, L) == pytest.approx(want, rel=1e-12)
+    g = er_cycle(40, 0.15, 2)  # L = 0 closed form on an irregular graph
+    d = g.degrees.astype(float)
+    for s, t in ((0, 1), (3, 27)):
+        want = 1 / d[s] ** 2 + 1 / d[t] ** 2 - (1 / d[s] - 1 / d[t]) ** 2 / g.n
+        assert ex.series_beta(g.row_ptr, g.col_idx, g.n, s, t, 0) == pytest.approx(want, rel=1e-13)
+    ref = exact.exact_beta(g.row_ptr, g.col_idx, g.n, 3, 27)  # converges to beta (non-bipartite)
+    assert ex.series_beta(g.row_ptr, g.col_idx, g.n, 3, 27, 400) == pytest.approx(ref, rel=1e-9)
+    # the many-pair form: the same closed forms, column by column
+    many = ex.series_beta_many(g.row_ptr, g.col_idx, g.n, np.array([0, 3]), np.array([1, 27]), 0)
+    for i, (s, t) in enumerate(((0, 1), (3, 27))):
+        want = 1 / d[s] ** 2 + 1 / d[t] ** 2 - (1 / d[s] - 1 / d[t]) ** 2 / g.n
+        assert many[i] == pytest.approx(want, rel=1e-13)
+    k = complete_graph(6)
+    many = ex.series_beta_many(k.row_ptr, k.col_idx, 6, np.array([0, 2]), np.array([5, 3]), 3)
+    np.testing.assert_allclose(many, 2.0 / 36 * (1 - (-1.0 / 5) ** 4) ** 2, rtol=1e-12)
+
+
+def test_exact_beta_checks():
+    check_exact_beta(exact)
+
+
+def test_series_checks():
+    assert not er_cycle(40, 0.15, 2).is_bipartite()
+    check_series(exact)

@@ -89,6 +89,24 @@ EXACT_MUTANTS = {
     # R_eff without the factor 2 on the cross term
     "reff_cross_factor": ("return float(lp[s, s] + lp[t, t] - 2.0 * lp[s, t])",
                           "return float(lp[s, s] + lp[t, t] - lp[s, t])"),
+    # (L + J/n)^-1 without subtracting J/n: not the pseudoinverse (beta alone would not notice)
+    "pinv_without_j": ("return np.linalg.inv(lap + j) - j", "return np.linalg.inv(lap + j)"),
+    # all-pairs beta with + on the cross term
+    "beta_matrix_cross_sign": ("return dg[:, None] + dg[None, :] - 2.0 * l2",
+                               "return dg[:, None] + dg[None, :] + 2.0 * l2"),
+    # beta from L^+ (e_s + e_t)
+    "beta_plus": ("x = lp[:, s] - lp[:, t]", "x = lp[:, s] + lp[:, t]"),
+    # series without its last term (L terms instead of L + 1)
+    "series_last_term_dropped": ("        x = (a @ x) / deg  # (P x)_i = (1/d_i) sum_{j in N(i)} x_j\n    h += x\n",
+                                 "        x = (a @ x) / deg  # (P x)_i = (1/d_i) sum_{j in N(i)} x_j\n"),
+    # A D^-1 x instead of D^-1 A x (the same on regular graphs only)
+    "series_transposed_step": ("x = (a @ x) / deg  # (P x)_i", "x = a @ (x / deg)  # (P x)_i"),
+    # series start b_st instead of D^-1 b_st
+    "series_start_without_degree": ("x[s] += 1.0 / deg[s]", "x[s] += 1.0"),
+    # ||h||^2 without the (1^T h)^2 / n term of Eq. tr-beta-exp-Liu
+    "series_no_mean_term": ("return sq - tot * tot / n", "return sq"),
+    # the many-pair series without its last term
+    "many_last_term_dropped": ("        x = (a @ x) / deg[:, None]\n    h += x\n", "        x = (a @ x) / deg[:, None]\n"),
 }
 
 
@@ -172,7 +190,8 @@ def test_planted_mistake_in_exact_is_caught(tmp_path, name):
         src = f.read()
     assert src.count(old) == 1, "mutation anchor not found in exact.py"
     mod = _load_exact_variant(src.replace(old, new), tmp_path, name)
-    failed = [fn.__name__ for fn in (exact_pins.check_effective_resistance, exact_pins.check_mixing_lambda)
+    failed = [fn.__name__ for fn in (exact_pins.check_effective_resistance, exact_pins.check_mixing_lambda,
+                                     exact_pins.check_exact_beta, exact_pins.check_series)
               if _pins_fail(fn, mod)]
     assert failed, f"no pin caught the planted mistake {name}"
 
@@ -184,3 +203,5 @@ def test_unmutated_exact_copy_passes(tmp_path):
         mod = _load_exact_variant(f.read(), tmp_path, "copy")
     exact_pins.check_effective_resistance(mod)
     exact_pins.check_mixing_lambda(mod)
+    exact_pins.check_exact_beta(mod)
+    exact_pins.check_series(mod)
