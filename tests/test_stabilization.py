@@ -29,6 +29,23 @@ def test_rule_on_a_prescribed_sequence(monkeypatch, oracle_lib):
     assert oracle.stabilized(None, 5, 5, 0.1, 64, 7)[:2] == (0.0, 1)
 
 
+def test_rule_is_relative_to_the_longer_level(monkeypatch, oracle_lib):
+    """The change is measured against |beta(2L)|, and level L runs on
+    level_seed(seed, L): 1.105 vs 1.0 at eps = 0.2 is within 0.1 * 1.105 but
+    not within 0.1 * 1.0, so the rule stops at L = 2."""
+    seq = {1: 1.0, 2: 1.105, 4: 5.0}
+    seen = {}
+
+    def fake_query(g, s, t, eps, L, seed, cfg=None, **kw):
+        seen[L] = seed
+        return {"beta": seq[L]}
+
+    monkeypatch.setattr(oracle, "query", fake_query)
+    beta, L_stop, levels = oracle.stabilized(None, 0, 1, 0.2, 4, 99)
+    assert (beta, L_stop) == (1.105, 2) and sorted(levels) == [1, 2]
+    assert seen == {L: oracle.level_seed(99, L) for L in (1, 2)}
+
+
 def test_level_seeds_differ_by_level(oracle_lib):
     seeds = {oracle.level_seed(12345, L) for L in (1, 2, 4, 8, 16)}
     assert len(seeds) == 5
