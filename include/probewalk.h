@@ -399,7 +399,9 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
  *
  * Runs the caller's sample batch (host arrays as in pw_query_batch, seeds may
  * be NULL, each query's s, t, L) with a FIXED budget of B = 16 probes per
- * block (8 queries give 4,736 probes at G = 37, enough to fill the GPU),
+ * block (8 queries give 4,736 probes at G = 37, enough to fill the GPU;
+ * the policy and window checks below run at the caller's own budget, where a
+ * sample of 32 queries or more stands for the batch far better than 8),
  * params' G, and R = 1024 replicas, each run after one untimed
  * warm-up: the per-visit kernel in its two register variants (compiler's
  * choice, or capped for 3 blocks of 256 per SM), keeping the faster; the
