@@ -427,8 +427,10 @@ pw_status pw_profile(pw_graph* g, int32_t enable, int32_t reset, pw_profile_stat
  * caller's budget under each L2 window of pw_graph_set_l2_window (none, the
  * gathered array, and on the split layout the node records; the windows the
  * device cannot set are skipped); the fastest window is kept if it beats no
- * window by 2 % or more, else none.  Call it with no server on g (server
- * launches carry the graph's window).  params as in
+ * window by 2 % or more, else none.  A kept window raises the CUDA
+ * context's persisting-L2 set-aside, which the rest of the process shares,
+ * until pw_graph_set_l2_window(g, 0) or pw_graph_free(g).  Call it with no
+ * server on g (server launches carry the graph's window).  params as in
  * pw_query (its walk_mode is ignored).  Errors as pw_query_batch; the
  * estimates of the runs are discarded. */
 typedef struct pw_tune_result {
